@@ -1,0 +1,406 @@
+"""Benchmark: LSD radix sort rate on GB300 (arXiv 1511.03404, Sec. 3-4 protocol).
+
+One step = one complete sort (upsweep + every digit pass) of one array of
+2^26 32-bit key + 32-bit value pairs; the steps cycle through the six input
+distributions of Sec. 4 (uniform, gaussian, zero, bucket, sorted,
+sorted descending).  As in Sec. 3, only the sort is timed: the data is
+already on the device (a device-to-device copy of the pristine input and an
+L2 flush run before each step, outside the events).  ``value`` is the whole
+job's sort rate in Gkeys/s.  ``e2e`` times the same sorts through the C ABI
+from pinned host buffers (host->device copy, sort, device->host copy).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank sorts its own replica (the sort does not
+shard); the slowest rank's time counts.  ``--impl reference`` times the CPU
+oracle (the slow, plain LSD counting sort) on bounded samples instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import inputs  # noqa: E402
+
+METRIC = "Gkeys/s & % HBM peak, radix sort 32/64-bit KV; batched vs plain; p99 latency"
+N_KEYS = 1 << 26
+DISTS = ("uniform", "gaussian", "zero", "bucket", "sorted", "sorted_desc")
+WORKLOAD = ("u32 key + u32 value (value = index) pairs, n=2^26, mt19937 seed 1, six "
+            "distributions (uniform, gaussian, zero, bucket, sorted, sorted_desc) one per step "
+            "in turn; LSD radix sort, 8-bit digits, 4 passes")
+L2_FLUSH_BYTES = 256 << 20
+
+# DRAM traffic of one onesweep launch from an ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum), keyed by the hash of the kernel sources it was taken
+# on; when the sources change the figure no longer applies and traffic is null.
+NCU_TRAFFIC = {}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1511_03404_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cuh", ".cu", ".h")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        return False
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for name, flag in zip(names, parts[5:9]):
+                if flag.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_inputs(n: int):
+    keys = {d: inputs.keys(np.uint32, d, n) for d in DISTS}
+    vals = inputs.values(np.uint32, n)
+    return keys, vals
+
+
+def cpu_oracle_rate(sample_n: int, dists=DISTS, budget_s: float = 12.0) -> dict:
+    """The oracle (single thread) on bounded samples of the same workload."""
+    import oracle
+
+    vals = inputs.values(np.uint32, sample_n)
+    done, t_total, used = 0, 0.0, []
+    for d in dists:
+        k = inputs.keys(np.uint32, d, sample_n)
+        t0 = time.perf_counter()
+        oracle.lsd_sort(k, vals)
+        t_total += time.perf_counter() - t0
+        done += sample_n
+        used.append(d)
+        if t_total > budget_s:
+            break
+    return {"value": done / t_total / 1e9, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
+            "sample": f"{len(used)} arrays of 2^{int(np.log2(sample_n))} u32 pairs "
+                      f"({', '.join(used)}), single-threaded C LSD counting sort, "
+                      f"{t_total:.1f} s"}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    sample_n = 1 << 22
+    vals = inputs.values(np.uint32, sample_n)
+    samples = [inputs.keys(np.uint32, DISTS[i % len(DISTS)], sample_n)
+               for i in range(args.warmup + args.steps)]
+    import oracle
+
+    for i in range(args.warmup):
+        oracle.lsd_sort(samples[i], vals)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        oracle.lsd_sort(samples[args.warmup + i], vals)
+    dt = time.perf_counter() - t0
+    value = args.steps * sample_n / dt / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Gkeys/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "reference_sample": "each step sorts one 2^22-pair "
+                   "sample of the workload, in turn over the six distributions, so that the "
+                   "run stays within minutes"},
+        "cpu_baseline": {"value": value, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} timed arrays of 2^22 u32 pairs"},
+        "e2e": {"value": value, "unit": "Gkeys/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    from paper_1511_03404_gb300 import rs
+
+    rank, world, local = dist_env()
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        pg = dist
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    n = args.n
+    keys_h, vals_h = make_inputs(n)
+    # pristine inputs on the device, plus the sort's double buffer and workspace
+    pristine = {d: torch.from_numpy(keys_h[d].view(np.int32)).to(dev) for d in DISTS}
+    vals0 = torch.from_numpy(vals_h.view(np.int32)).to(dev)
+    k, v = torch.empty_like(vals0), torch.empty_like(vals0)
+    ka, va = torch.empty_like(vals0), torch.empty_like(vals0)
+    st, nbytes = rs.rs_workspace_bytes(4, 4, n, 0, 32)
+    rs.check(st, "rs_workspace_bytes")
+    ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    h = stream.cuda_stream
+
+    def one_sort(i, ev0=None, ev1=None):
+        d = DISTS[i % len(DISTS)]
+        k.copy_(pristine[d])
+        v.copy_(vals0)
+        flush.fill_(i & 0xFF)
+        if ev0 is not None:
+            ev0.record(stream)
+        st, in_alt = rs.rs_sort_pairs_u32(k.data_ptr(), v.data_ptr(), ka.data_ptr(),
+                                          va.data_ptr(), n, 0, 32, ws.data_ptr(), ws.numel(), h)
+        if ev1 is not None:
+            ev1.record(stream)
+        rs.check(st, "rs_sort_pairs_u32")
+        return d, in_alt
+
+    # correctness of the timed configuration: every distribution once, checked
+    # against the properties that fix a stable sort (sorted keys, values are a
+    # permutation, keys_in[vals_out] == keys_out, equal keys keep index order)
+    for i in range(len(DISTS)):
+        d, in_alt = one_sort(i)
+        st, info = rs.rs_workspace_status(ws.data_ptr(), h)
+        rs.check(st, "device status")
+        if i == 0 and rank == 0:
+            ok = check_sorted(torch, (ka if in_alt else k), (va if in_alt else v), pristine[d])
+            if not ok:
+                raise SystemExit("bench: sorted output failed its property check")
+
+    for i in range(args.warmup):
+        one_sort(i)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    rs.check(rs.rs_profile_begin(16 * args.steps + 16), "rs_profile_begin")
+    with ClockSampler(dev.index or 0) as clocks:
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            one_sort(i, starts[i], ends[i])
+        torch.cuda.synchronize()
+    st, prof = rs.rs_profile_end()
+    rs.check(st, "rs_profile_end")
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    if pg:
+        t = torch.tensor([total_ms], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps * n / (total_ms / 1e3) / 1e9
+
+    # end to end through the C ABI: pinned host -> device, sort, device -> host
+    e2e = e2e_rate(torch, rs, keys_h, vals_h, n, dev, ws, args)
+    if pg:
+        t = torch.tensor([e2e["ms_per_step"]], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e["value"] = world * n / (float(t.item()) / 1e3) / 1e9
+
+    if rank != 0:
+        if pg:
+            pg.destroy_process_group()
+        return 0
+
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs")
+    os_p = prof["onesweep"]
+    achieved = (os_p["bytes"] / 1e9) / (os_p["ms"] / 1e3) if os_p["ms"] > 0 else None
+    launches = sum(p["launches"] for p in prof.values())
+    traffic = None
+    src = kernel_source_hash()
+    t = NCU_TRAFFIC.get(src)
+    if t is not None:
+        traffic = t
+    line = {
+        "metric": METRIC, "value": value, "unit": "Gkeys/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "digit_bits": 8,
+                   "l2": "256 MiB written before every timed sort; inputs (512 MiB) exceed L2",
+                   "timing": "CUDA events around each sort call on its stream",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": (achieved / hbm) if (achieved and hbm) else None,
+                     "traffic": traffic, "kernel": "k_onesweep (one digit pass)",
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if hbm else None,
+                     "algorithmic_bytes_per_launch": "2 n (4 + 4) for a pass that moves data"},
+        "per_kernel": {k_: {"launches": p["launches"], "ms": p["ms"],
+                            "GB/s": (p["bytes"] / 1e9) / (p["ms"] / 1e3) if p["ms"] else None}
+                       for k_, p in prof.items() if p["launches"]},
+        "per_dist_ms": {d: statistics.mean(step_ms[i::len(DISTS)])
+                        for i, d in enumerate(DISTS) if step_ms[i::len(DISTS)]},
+        "cpu_baseline": None,
+        "e2e": {"value": e2e["value"], "unit": "Gkeys/s",
+                "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]},
+        "gpu_launches": launches,
+        "clocks": clocks.summary(),
+        "kernel_source": src,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_oracle_rate(1 << 24)
+        line["cpu_baseline"]["host"] = host_description()
+    print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+def host_description() -> str:
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for l_ in f:
+                if l_.lower().startswith(("model name", "cpu part")):
+                    model = l_.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return f"{os.cpu_count()} cores {model}".strip()
+
+
+def check_sorted(torch, k_out, v_out, k_in) -> bool:
+    ko = k_out.to(torch.int64) & 0xFFFFFFFF
+    if not bool((ko[1:] >= ko[:-1]).all()):
+        return False
+    idx = v_out.to(torch.int64)
+    if not bool((torch.sort(idx).values == torch.arange(idx.numel(), device=idx.device)).all()):
+        return False
+    if not bool((k_in[idx] == k_out).all()):
+        return False
+    eq = ko[1:] == ko[:-1]
+    return bool((idx[1:][eq] > idx[:-1][eq]).all())
+
+
+def e2e_rate(torch, rs, keys_h, vals_h, n, dev, ws, args) -> dict:
+    """Host -> device copy, sort, device -> host copy, per step, through the C ABI."""
+    hk = {d: torch.from_numpy(keys_h[d].view(np.int32)).pin_memory() for d in DISTS}
+    hv = torch.from_numpy(vals_h.view(np.int32)).pin_memory()
+    ok = torch.empty(n, dtype=torch.int32).pin_memory()
+    ov = torch.empty(n, dtype=torch.int32).pin_memory()
+    k = torch.empty(n, dtype=torch.int32, device=dev)
+    v, ka, va = torch.empty_like(k), torch.empty_like(k), torch.empty_like(k)
+    stream = torch.cuda.current_stream(dev)
+    h = stream.cuda_stream
+
+    def step(i):
+        d = DISTS[i % len(DISTS)]
+        k.copy_(hk[d], non_blocking=True)
+        v.copy_(hv, non_blocking=True)
+        st, in_alt = rs.rs_sort_pairs_u32(k.data_ptr(), v.data_ptr(), ka.data_ptr(),
+                                          va.data_ptr(), n, 0, 32, ws.data_ptr(), ws.numel(), h)
+        rs.check(st, "rs_sort_pairs_u32")
+        ok.copy_(ka if in_alt else k, non_blocking=True)
+        ov.copy_(va if in_alt else v, non_blocking=True)
+
+    steps = max(3, min(args.steps, 12))
+    for i in range(3):
+        step(i)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for i in range(steps):
+        step(i)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / steps
+    return {"value": n / (ms / 1e3) / 1e9, "ms_per_step": ms, "h2d": 2 * 4 * n, "d2h": 2 * 4 * n}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=6)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--n", type=int, default=N_KEYS)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

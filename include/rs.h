@@ -1,0 +1,215 @@
+/*
+ * rs -- LSD radix sort for NVIDIA GB300 (sm_103a).  C ABI.
+ *
+ * The method is the parallel LSD radix sort of Bozidar & Dobravec,
+ * "Comparison of parallel sorting algorithms" (arXiv 1511.03404), Sec. 2.6:
+ * keys are split into d digits of r bits; the sequence is sorted one digit
+ * at a time from the least to the most significant digit, each time with a
+ * stable counting sort (digit histogram, exclusive scan of the histogram,
+ * stable scatter).  Sec. 1 and Sec. 3 ask for arbitrary lengths and for four
+ * data types: 32-bit keys, 32-bit key-value pairs, 64-bit keys and 64-bit
+ * key-value pairs.
+ *
+ * Conventions shared by every entry point below:
+ *   - Order: ascending unsigned order of the key bits [begin_bit, end_bit).
+ *     Bits outside that range are ignored (but kept).  The sort is stable:
+ *     elements with equal key bits keep their input order.
+ *   - Pairs are structure-of-arrays: keys[i] and vals[i] belong together.
+ *     Values have the width of the keys (u32 with u32 keys, u64 with u64).
+ *   - Device pointers.  keys/vals/keys_alt/vals_alt, the workspace and every
+ *     other buffer named "d_" or "device" are device memory of the current
+ *     CUDA device, owned by the caller; the library never allocates, frees
+ *     or retains them past the call.  Keys and values must be aligned to
+ *     their element size; the workspace to 256 bytes.
+ *   - Double buffering.  keys_alt/vals_alt are caller-owned buffers of the
+ *     same size as keys/vals.  On return *result_in_alt tells where the
+ *     sorted sequence will be: 0 = keys/vals, 1 = keys_alt/vals_alt.  The
+ *     other pair of buffers holds unspecified data afterwards.  The input is
+ *     not preserved.
+ *   - Asynchrony.  Sorts are enqueued on `stream` (a cudaStream_t; NULL is
+ *     the legacy default stream) and return before the work completes.
+ *     The call itself never synchronizes.  All kernels of one call go on
+ *     that one stream, so a call can be captured into a CUDA graph.
+ *   - Errors.  Every call returns an rs_status.  Argument errors are found on
+ *     the host before anything is enqueued (RS_ERR_INVALID,
+ *     RS_ERR_WORKSPACE).  Launch failures give RS_ERR_CUDA.  Errors that can
+ *     only be seen on the device (a bounded wait that ran out, an index
+ *     check that failed) are recorded in a status word inside the workspace;
+ *     read it with rs_workspace_status() after the stream's work is done.
+ *     The library never aborts, traps or hangs: every device-side wait is
+ *     bounded in time.
+ *   - Limits: n <= RS_MAX_N.  0 <= begin_bit <= end_bit <= key bits.
+ */
+#ifndef RS_H_
+#define RS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t. */
+typedef struct CUstream_st* rs_stream_t;
+
+/* Largest supported number of elements in one array or one segment.  The
+ * look-back status words carry a 30-bit running count. */
+#define RS_MAX_N ((size_t)((1u << 30) - 1u))
+
+typedef enum rs_status {
+  RS_OK = 0,
+  RS_ERR_INVALID = 1,   /* bad argument: null pointer, misalignment, size or bit range */
+  RS_ERR_NOMEM = 2,     /* an allocation the call needed (server pool) failed */
+  RS_ERR_CUDA = 3,      /* a CUDA runtime call or kernel launch failed */
+  RS_ERR_TIMEOUT = 4,   /* a bounded device-side wait (decoupled look-back) ran out */
+  RS_ERR_BUSY = 5,      /* server: request not admitted now (queue full / over budget) */
+  RS_ERR_WORKSPACE = 6, /* workspace missing, too small or misaligned */
+  RS_ERR_DEVICE = 7,    /* a device-side index check failed; output not valid */
+  RS_ERR_CANCELLED = 8, /* server: request cancelled before it ran */
+  RS_ERR_NOT_FOUND = 9  /* server: unknown handle */
+} rs_status;
+
+/* Human-readable name of a status code (static string). */
+const char* rs_status_string(rs_status s);
+
+/* Library version as "major.minor.patch" (static string). */
+const char* rs_version(void);
+
+/*
+ * Tuning parameters.  radix_bits is the digit width r of Sec. 2.6; the sorted
+ * result does not depend on it.  variant selects one of the compiled tile
+ * shapes (threads per CTA x keys per thread), see rs_variant_info().
+ * A zero / negative field means "let the library choose" (the tuned table).
+ */
+typedef struct rs_config {
+  int radix_bits; /* 0: library choice; else one of the compiled widths */
+  int variant;    /* -1: library choice; else an index from rs_variant_info */
+} rs_config;
+
+/* Number of compiled tile variants for (key_bytes, val_bytes); val_bytes 0 = keys only. */
+int rs_num_variants(int key_bytes, int val_bytes);
+
+/*
+ * Describe variant `index` of (key_bytes, val_bytes): digit width, threads
+ * per CTA, keys per thread, and kind (0 = multi-CTA onesweep, 1 = one CTA
+ * sorting the whole array in shared memory; max_n bounds the latter).
+ */
+rs_status rs_variant_info(int key_bytes, int val_bytes, int index, int* radix_bits,
+                          int* threads, int* items_per_thread, int* kind, size_t* max_n);
+
+/*
+ * Workspace bytes a sort of n elements over [begin_bit, end_bit) needs with
+ * configuration cfg (NULL = library choice).  The sort entry points with the
+ * same arguments accept any workspace at least this large.
+ */
+rs_status rs_workspace_bytes(int key_bytes, int val_bytes, size_t n, int begin_bit, int end_bit,
+                             const rs_config* cfg, size_t* bytes);
+
+/*
+ * Sort 32-bit keys (Sec. 2.6 over 32-bit keys, Sec. 3).
+ *   keys      [n] u32, device: input; may receive the output (see result_in_alt)
+ *   keys_alt  [n] u32, device: the second buffer of the double buffer
+ *   ws        device workspace of at least rs_workspace_bytes(4, 0, ...) bytes
+ *   result_in_alt  host int, set before return: 1 if the sorted keys end in keys_alt
+ */
+rs_status rs_sort_keys_u32(uint32_t* keys, uint32_t* keys_alt, size_t n, int begin_bit,
+                           int end_bit, void* ws, size_t ws_bytes, rs_stream_t stream,
+                           int* result_in_alt);
+
+/* Sort 64-bit keys (Sec. 2.6 over 64-bit keys, Sec. 3).  As rs_sort_keys_u32. */
+rs_status rs_sort_keys_u64(uint64_t* keys, uint64_t* keys_alt, size_t n, int begin_bit,
+                           int end_bit, void* ws, size_t ws_bytes, rs_stream_t stream,
+                           int* result_in_alt);
+
+/*
+ * Sort 32-bit key-value pairs by key (Sec. 2.6, Sec. 3), stable.
+ *   vals / vals_alt  [n] u32 device buffers that travel with keys / keys_alt.
+ */
+rs_status rs_sort_pairs_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
+                            uint32_t* vals_alt, size_t n, int begin_bit, int end_bit, void* ws,
+                            size_t ws_bytes, rs_stream_t stream, int* result_in_alt);
+
+/* Sort 64-bit key-value pairs by key (Sec. 2.6, Sec. 3), stable. */
+rs_status rs_sort_pairs_u64(uint64_t* keys, uint64_t* vals, uint64_t* keys_alt,
+                            uint64_t* vals_alt, size_t n, int begin_bit, int end_bit, void* ws,
+                            size_t ws_bytes, rs_stream_t stream, int* result_in_alt);
+
+/*
+ * Generic form of the four sorts above with an explicit configuration.
+ * key_bytes is 4 or 8; val_bytes is 0 (keys only) or equal to key_bytes.
+ * vals / vals_alt must be NULL when val_bytes is 0.
+ */
+rs_status rs_sort(int key_bytes, int val_bytes, void* keys, void* vals, void* keys_alt,
+                  void* vals_alt, size_t n, int begin_bit, int end_bit, const rs_config* cfg,
+                  void* ws, size_t ws_bytes, rs_stream_t stream, int* result_in_alt);
+
+/*
+ * Digit histograms and their exclusive scans, the first two steps of each
+ * counting sort of Sec. 2.6, for every digit pass at once.
+ *   keys         [n] device keys of key_bytes (4 or 8); not modified
+ *   d_counts     [passes * 2^radix_bits] u32 device: counts[p][v] = number of
+ *                keys whose digit p equals v
+ *   d_offsets    [passes * 2^radix_bits] u32 device: offsets[p][v] =
+ *                sum of counts[p][u] over u < v
+ *   d_exec_mask  [1] u32 device: bit p set when pass p moves data (no single
+ *                digit value holds all n keys), after the parity rule that
+ *                keeps the number of moving passes congruent to `passes` mod 2
+ * passes = ceil((end_bit - begin_bit) / radix_bits).  Uses workspace like a
+ * sort of the same keys.
+ */
+rs_status rs_digit_counts(int key_bytes, const void* keys, size_t n, int begin_bit, int end_bit,
+                          int radix_bits, uint32_t* d_counts, uint32_t* d_offsets,
+                          uint32_t* d_exec_mask, void* ws, size_t ws_bytes, rs_stream_t stream);
+
+/*
+ * Wait for `stream` and report the device-side status of the last call that
+ * used workspace `ws`: RS_OK, RS_ERR_TIMEOUT or RS_ERR_DEVICE (RS_ERR_CUDA if
+ * the synchronization itself failed).  *info (may be NULL) receives the tile
+ * or pass the device reported.
+ */
+rs_status rs_workspace_status(const void* ws, rs_stream_t stream, uint32_t* info);
+
+/* ---- per-kernel timing (CUDA events recorded on the sort's stream) ---- */
+
+/* Kinds of kernels the library launches. */
+typedef enum rs_kernel_kind {
+  RS_KERNEL_UPSWEEP = 0, /* digit histograms of all passes + scan */
+  RS_KERNEL_ONESWEEP = 1, /* one digit pass: rank, look-back, stable scatter */
+  RS_KERNEL_SMALL = 2,   /* whole array sorted by one CTA in shared memory */
+  RS_KERNEL_SEGMENTED = 3, /* batched segments */
+  RS_KERNEL_KINDS = 4
+} rs_kernel_kind;
+
+/*
+ * Start recording: every later kernel launch of this library on this host
+ * thread is bracketed by CUDA events (up to `capacity` launches).  Calling
+ * it again discards earlier records.
+ */
+rs_status rs_profile_begin(int capacity);
+
+/*
+ * Stop recording, wait for the recorded events and return, per kernel kind,
+ * the number of launches, their summed duration in milliseconds and their
+ * summed algorithmic bytes (reads + writes the method needs: for a onesweep
+ * pass 2 n (key bytes + value bytes), for the upsweep n key bytes).  Arrays
+ * have RS_KERNEL_KINDS entries; any may be NULL.
+ */
+rs_status rs_profile_end(int* launches, double* ms, double* bytes);
+
+/* ---- fault injection for tests (host-set, off by default) ---- */
+
+typedef enum rs_debug_knob {
+  RS_DEBUG_TIMEOUT_NS = 0,        /* look-back wait limit in ns (default 2e9) */
+  RS_DEBUG_DROP_PUBLISH_TILE = 1, /* tile that never publishes its look-back status; -1 off */
+  RS_DEBUG_DROP_PUBLISH_PASS = 2  /* pass in which that tile stays silent */
+} rs_debug_knob;
+
+/* Set a knob for later calls from any thread; returns RS_ERR_INVALID for an unknown knob. */
+rs_status rs_debug_set(rs_debug_knob knob, long long value);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RS_H_ */

@@ -1,0 +1,67 @@
+// Host/device shared definitions of the rs library: workspace layout, the
+// control block the kernels communicate through, and kernel arguments.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+namespace rs {
+
+// Look-back status word of one (tile, digit): 2 flag bits + a 30-bit count.
+constexpr uint32_t kFlagShift = 30;
+constexpr uint32_t kFlagAgg = 1u << kFlagShift;  // count of this tile only
+constexpr uint32_t kFlagInc = 2u << kFlagShift;  // count of all tiles up to and including this one
+constexpr uint32_t kFlagErr = 3u << kFlagShift;  // this tile gave up; successors give up too
+constexpr uint32_t kFlagMask = 3u << kFlagShift;
+constexpr uint32_t kValueMask = (1u << kFlagShift) - 1u;
+
+constexpr int kMaxPasses = 16;  // 64-bit keys at 4-bit digits
+
+// Device status codes (the values of rs_status).
+constexpr uint32_t kDevOk = 0;
+constexpr uint32_t kDevTimeout = 4;
+constexpr uint32_t kDevIndex = 7;
+
+// The first 256 bytes of every workspace.
+struct Ctrl {
+  uint32_t error;       // 0, or the first device status code reported
+  uint32_t error_info;  // tile (or pass) that reported it
+  uint32_t hist_ticket; // upsweep CTAs that have finished
+  uint32_t exec_mask;   // bit p: pass p moves the data (written by the upsweep's last CTA)
+  uint32_t tile_counter[kMaxPasses];  // dynamic tile ids of each pass
+  uint32_t reserved[64 - 4 - kMaxPasses];
+};
+static_assert(sizeof(Ctrl) == 256, "Ctrl must be 256 bytes");
+
+// Test-only fault injection and the bound on every device-side wait.
+struct Knobs {
+  uint64_t timeout_ns;     // a look-back wait gives up after this long
+  int32_t drop_tile;       // this tile never publishes its status (-1: off)
+  int32_t drop_pass;       // ... in this pass
+};
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Workspace of one onesweep sort with `passes` digit passes, radix 2^r and
+// `tiles` tiles per pass:
+//   [0, 256)            Ctrl
+//   counts   u32 [passes][radix]    digit histograms (atomics; zeroed per call)
+//   offsets  u32 [passes][radix]    exclusive scans of the histograms
+//   status   u32 [passes][tiles][radix]  look-back words (zeroed by the upsweep)
+struct Layout {
+  size_t counts, offsets, status, status_bytes, total, memset_bytes;
+};
+
+inline Layout onesweep_layout(int passes, int radix_bits, size_t tiles) {
+  Layout L;
+  const size_t radix = size_t(1) << radix_bits;
+  L.counts = 256;
+  L.offsets = align_up(L.counts + size_t(passes) * radix * 4, 256);
+  L.status = align_up(L.offsets + size_t(passes) * radix * 4, 256);
+  L.status_bytes = align_up(size_t(passes) * tiles * radix * 4, 256);
+  L.total = L.status + L.status_bytes;
+  L.memset_bytes = L.offsets;  // Ctrl + counts
+  return L;
+}
+
+}  // namespace rs

@@ -1,0 +1,15 @@
+// Compiled variants of the sort for key-value pairs, uint32_t keys.
+#include "rs_launch.cuh"
+
+namespace rs {
+
+const Variant* variants_kv32(int* count) {
+  static const Variant table[] = {
+      OnesweepSort<uint32_t, 4, 8, 256, 16, 2>::describe(),
+      SmallSort<uint32_t, 4, 8, 512, 16>::describe(),
+  };
+  *count = int(sizeof(table) / sizeof(table[0]));
+  return table;
+}
+
+}  // namespace rs

@@ -1,0 +1,15 @@
+// Compiled variants of the sort for key-value pairs, uint64_t keys.
+#include "rs_launch.cuh"
+
+namespace rs {
+
+const Variant* variants_kv64(int* count) {
+  static const Variant table[] = {
+      OnesweepSort<uint64_t, 8, 8, 256, 12, 2>::describe(),
+      SmallSort<uint64_t, 8, 8, 512, 16>::describe(),
+  };
+  *count = int(sizeof(table) / sizeof(table[0]));
+  return table;
+}
+
+}  // namespace rs

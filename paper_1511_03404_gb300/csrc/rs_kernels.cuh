@@ -1,0 +1,573 @@
+// Device kernels of the LSD radix sort (arXiv 1511.03404, Sec. 2.6).
+//
+// One sort = one upsweep + one onesweep launch per digit pass:
+//   k_upsweep   reads the keys once and builds the digit histogram of every
+//               pass (the "count" step of each counting sort); its last CTA
+//               takes the exclusive scan of each histogram (the "prefix"
+//               step) and decides which passes move data.
+//   k_onesweep  one digit pass: the tile's keys are ranked within the tile
+//               (stable: warp-major, then item, then lane order), the tile's
+//               digit counts are published for the following tiles, the
+//               tile's global digit offsets come from a decoupled look-back
+//               over the preceding tiles, and the tile is scattered through
+//               shared memory so that each digit run is written contiguously
+//               (the stable "scatter" step).
+//   k_small_sort  arrays that fit one tile: all passes in one CTA, in shared
+//               memory, in a single launch.
+// All arithmetic is on unsigned integers; results are exact.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <type_traits>
+
+#include "rs_common.h"
+
+namespace rs {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+template <int VB>
+using ValT = typename std::conditional<VB == 8, uint64_t, uint32_t>::type;
+
+// ---------------------------------------------------------------- helpers
+
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+template <class K>
+__device__ __forceinline__ uint32_t digit_of(K key, uint32_t shift, uint32_t mask) {
+  return static_cast<uint32_t>(key >> shift) & mask;
+}
+
+// Record the first device-side error of a call (later ones are dropped).
+__device__ __forceinline__ void report_error(Ctrl* ctrl, uint32_t code, uint32_t info) {
+  if (atomicCAS(&ctrl->error, 0u, code) == 0u) atomicExch(&ctrl->error_info, info);
+}
+
+__device__ __forceinline__ uint32_t warp_inclusive_scan(uint32_t x, int lane) {
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    uint32_t y = __shfl_up_sync(kFull, x, off);
+    if (lane >= off) x += y;
+  }
+  return x;
+}
+
+// Exclusive scan of one value per thread across the CTA.  s_tot holds 32
+// words.  Every thread must call it; the caller separates two calls with a
+// barrier.
+template <int THREADS>
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t* s_tot) {
+  constexpr int WARPS = THREADS / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t inc = warp_inclusive_scan(x, lane);
+  if (lane == 31) s_tot[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t t = lane < WARPS ? s_tot[lane] : 0u;
+    const uint32_t ti = warp_inclusive_scan(t, lane);
+    s_tot[lane] = ti - t;
+  }
+  __syncthreads();
+  return inc - x + s_tot[warp];
+}
+
+// Wait (bounded) until a look-back status word has a flag.  Returns the word,
+// or kFlagErr when the wait ran out or another CTA already reported an error.
+static __device__ __noinline__ uint32_t wait_status(const uint32_t* p, Ctrl* ctrl, uint64_t timeout_ns,
+                                             uint32_t tile) {
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 1;; ++it) {
+    const uint32_t s = ld_relaxed(p);
+    if (s & kFlagMask) return s;
+    if ((it & 63u) == 0u) {
+      if (ld_relaxed(&ctrl->error) != 0u) return kFlagErr;
+      if (global_ns() - t0 > timeout_ns) {
+        report_error(ctrl, kDevTimeout, tile);
+        return kFlagErr;
+      }
+    }
+  }
+}
+
+// --------------------------------------------------------------- upsweep
+
+// Digit histograms of every pass in one read of the keys, then (last CTA)
+// the exclusive scan of each and the set of passes that move data.
+//
+// Shared counters are 16-bit halves of 32-bit words laid out
+// [pass][digit/2][lane]: lane l only touches bank l, so a warp's 32
+// increments never conflict on a bank whatever the digits are (the zero and
+// sorted distributions included).  The 16-bit counters are drained into the
+// global counts before they can overflow.
+template <class K, int RADIX_BITS, int THREADS, int MAXP>
+__global__ void __launch_bounds__(THREADS)
+    k_upsweep(const K* __restrict__ keys, uint32_t n, int begin_bit, int end_bit, int passes,
+              uint32_t* __restrict__ counts, uint32_t* __restrict__ offsets,
+              Ctrl* __restrict__ ctrl, uint4* __restrict__ zero_base, uint64_t zero_vec4) {
+  constexpr int RADIX = 1 << RADIX_BITS;
+  constexpr int HALF = RADIX / 2;
+  constexpr int WARPS = THREADS / 32;
+  constexpr int VEC = 16 / int(sizeof(K));
+  constexpr int UNROLL = 4;
+  // each (pass, digit pair, lane) half-word gains at most WARPS*VEC*UNROLL
+  // per round, plus 2 from the scalar head and tail
+  constexpr uint32_t FLUSH_ROUNDS = (65535u - 2u) / uint32_t(WARPS * VEC * UNROLL);
+  static_assert(RADIX <= THREADS, "one thread per digit in the scan");
+  static_assert(FLUSH_ROUNDS >= 1, "block too large for 16-bit counters");
+
+  extern __shared__ uint32_t sh[];  // [passes][HALF][32]
+  __shared__ uint32_t s_tot[32];
+  __shared__ int s_last;
+
+  const int tid = threadIdx.x, lane = tid & 31;
+  uint32_t shiftp[MAXP], maskp[MAXP];
+#pragma unroll
+  for (int p = 0; p < MAXP; ++p) {
+    const int lo = begin_bit + p * RADIX_BITS;
+    const int hi = min(lo + RADIX_BITS, end_bit);
+    shiftp[p] = p < passes ? uint32_t(lo) : 0u;
+    maskp[p] = p < passes ? ((1u << (hi - lo)) - 1u) : 0u;
+  }
+  const int words = passes * HALF * 32;
+  for (int i = tid; i < words; i += THREADS) sh[i] = 0u;
+  __syncthreads();
+
+  auto count_key = [&](K k) {
+#pragma unroll
+    for (int p = 0; p < MAXP; ++p) {
+      if (p < passes) {
+        const uint32_t d = digit_of(k, shiftp[p], maskp[p]);
+        atomicAdd(&sh[(p * HALF + int(d >> 1)) * 32 + lane], 1u << ((d & 1u) << 4));
+      }
+    }
+  };
+
+  auto flush = [&]() {
+    __syncthreads();
+    for (int w = tid; w < passes * HALF; w += THREADS) {
+      uint32_t lo = 0u, hi = 0u;
+      uint32_t* row = sh + w * 32;
+#pragma unroll 8
+      for (int l = 0; l < 32; ++l) {
+        const int c = (l + lane) & 31;  // rotated: lanes read distinct banks
+        const uint32_t x = row[c];
+        row[c] = 0u;
+        lo += x & 0xFFFFu;
+        hi += x >> 16;
+      }
+      const int p = w / HALF, d = (w - p * HALF) * 2;
+      if (lo) atomicAdd(&counts[p * RADIX + d], lo);
+      if (hi) atomicAdd(&counts[p * RADIX + d + 1], hi);
+    }
+    __syncthreads();
+  };
+
+  // 16-byte aligned body, scalar head and tail
+  const uintptr_t addr = reinterpret_cast<uintptr_t>(keys);
+  uint32_t head = uint32_t(((16u - (addr & 15u)) & 15u) / sizeof(K));
+  if (head > n) head = n;
+  const uint32_t nvec = (n - head) / VEC;
+  const uint32_t tail = head + nvec * VEC;
+  if (blockIdx.x == 0) {
+    if (uint32_t(tid) < head) count_key(keys[tid]);
+    if (uint32_t(tid) < n - tail) count_key(keys[tail + tid]);
+  }
+  const uint4* vp = reinterpret_cast<const uint4*>(keys + head);
+  const uint32_t stride = gridDim.x * THREADS;
+  const uint32_t per_round = stride * UNROLL;
+  const uint32_t rounds = (nvec + per_round - 1u) / per_round;
+  uint32_t since = 0;
+  for (uint32_t r = 0; r < rounds; ++r) {
+    const uint32_t base = r * per_round + blockIdx.x * THREADS + tid;
+    uint4 buf[UNROLL];
+#pragma unroll
+    for (int u = 0; u < UNROLL; ++u) {
+      const uint32_t i = base + uint32_t(u) * stride;
+      if (i < nvec) buf[u] = vp[i];
+    }
+#pragma unroll
+    for (int u = 0; u < UNROLL; ++u) {
+      const uint32_t i = base + uint32_t(u) * stride;
+      if (i < nvec) {
+        const K* ks = reinterpret_cast<const K*>(&buf[u]);
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) count_key(ks[e]);
+      }
+    }
+    if (++since == FLUSH_ROUNDS && r + 1 < rounds) {
+      flush();
+      since = 0;
+    }
+  }
+  flush();
+
+  // clear the look-back status words of every pass of this call
+  for (uint64_t i = uint64_t(blockIdx.x) * THREADS + tid; i < zero_vec4; i += stride)
+    zero_base[i] = make_uint4(0u, 0u, 0u, 0u);
+
+  // last CTA: scan each histogram, choose the passes that move data
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) s_last = (atomicAdd(&ctrl->hist_ticket, 1u) == gridDim.x - 1u);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  uint32_t exec = 0u;
+  for (int p = 0; p < passes; ++p) {
+    const uint32_t c = tid < RADIX ? ld_relaxed(&counts[p * RADIX + tid]) : 0u;
+    const uint32_t e = block_exclusive_scan<THREADS>(c, s_tot);
+    if (tid < RADIX) offsets[p * RADIX + tid] = e;
+    // a pass in which one digit value holds every key leaves the order as it is
+    const int one_digit = __syncthreads_or(tid < RADIX && c == n);
+    if (!one_digit) exec |= 1u << p;
+  }
+  if (tid == 0) {
+    // the sorted data must end in the buffer the host named (pass count
+    // parity): if skipping changed the parity, the lowest skipped pass runs
+    if ((__popc(exec) & 1) != (passes & 1)) {
+      const uint32_t skipped = ~exec & ((1u << passes) - 1u);
+      exec |= skipped & (0u - skipped);
+    }
+    ctrl->exec_mask = exec;
+  }
+}
+
+// -------------------------------------------------------------- onesweep
+
+template <class K, int VB, int RADIX_BITS, int THREADS, int ITEMS>
+struct OnesweepSmem {
+  static constexpr int RADIX = 1 << RADIX_BITS;
+  static constexpr int WARPS = THREADS / 32;
+  static constexpr int TILE = THREADS * ITEMS;
+  static constexpr int ELEM = (int(sizeof(K)) > VB) ? int(sizeof(K)) : VB;
+  static constexpr int WH = 0;                              // u32 [WARPS][RADIX]
+  static constexpr int CNT = WH + WARPS * RADIX * 4;       // u32 [RADIX] tile counts
+  static constexpr int TSTART = CNT + RADIX * 4;           // u32 [RADIX] tile digit starts
+  static constexpr int GBASE = TSTART + RADIX * 4;         // u32 [RADIX] global base
+  static constexpr int TOT = GBASE + RADIX * 4;            // u32 [32]
+  static constexpr int MISC = TOT + 32 * 4;                // u32 [4]: tile, abort
+  static constexpr int STAGE = (MISC + 16 + 15) / 16 * 16; // TILE elements
+  static constexpr int BYTES = STAGE + TILE * ELEM;
+};
+
+// One digit pass over one tile per CTA.  The grid has one CTA per tile; tile
+// ids come from an atomic counter so that a tile's predecessors have always
+// started before it (forward progress of the look-back).
+template <class K, int VB, int RADIX_BITS, int THREADS, int ITEMS, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB)
+    k_onesweep(K* __restrict__ k0, K* __restrict__ k1, ValT<VB>* __restrict__ v0,
+               ValT<VB>* __restrict__ v1, uint32_t n, int pass, uint32_t shift, uint32_t mask,
+               const uint32_t* __restrict__ pass_offsets, uint32_t* __restrict__ status,
+               Ctrl* __restrict__ ctrl, Knobs knobs) {
+  using V = ValT<VB>;
+  using S = OnesweepSmem<K, VB, RADIX_BITS, THREADS, ITEMS>;
+  constexpr int RADIX = S::RADIX, WARPS = S::WARPS, TILE = S::TILE;
+  static_assert(RADIX <= THREADS, "one thread per digit");
+
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint32_t* s_wh = reinterpret_cast<uint32_t*>(smem + S::WH);
+  uint32_t* s_cnt = reinterpret_cast<uint32_t*>(smem + S::CNT);
+  uint32_t* s_tstart = reinterpret_cast<uint32_t*>(smem + S::TSTART);
+  uint32_t* s_gbase = reinterpret_cast<uint32_t*>(smem + S::GBASE);
+  uint32_t* s_tot = reinterpret_cast<uint32_t*>(smem + S::TOT);
+  uint32_t* s_misc = reinterpret_cast<uint32_t*>(smem + S::MISC);
+
+  const uint32_t exec = ctrl->exec_mask;
+  if (!((exec >> pass) & 1u)) return;  // every key has the same digit: nothing moves
+  const bool from_alt = (__popc(exec & ((1u << pass) - 1u)) & 1) != 0;
+  const K* __restrict__ ksrc = from_alt ? k1 : k0;
+  K* __restrict__ kdst = from_alt ? k0 : k1;
+  const V* __restrict__ vsrc = from_alt ? v1 : v0;
+  V* __restrict__ vdst = from_alt ? v0 : v1;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) {
+    s_misc[0] = atomicAdd(&ctrl->tile_counter[pass], 1u);
+    s_misc[1] = 0u;
+    s_misc[2] = ld_relaxed(&ctrl->error);  // an earlier pass of this call gave up
+  }
+  for (int i = tid; i < WARPS * RADIX; i += THREADS) s_wh[i] = 0u;
+  __syncthreads();
+  if (s_misc[2] != 0u) return;  // CTA-uniform
+  const uint32_t tile = s_misc[0];
+  const uint32_t tile_base = tile * uint32_t(TILE);
+  const uint32_t tile_len = min(uint32_t(TILE), n - tile_base);
+
+  // load: warp w owns tile elements [w*ITEMS*32, (w+1)*ITEMS*32), item j of
+  // lane l is element w*ITEMS*32 + j*32 + l (coalesced per item)
+  K key[ITEMS];
+  V val[ITEMS];
+  const uint32_t wbase = tile_base + uint32_t(warp * ITEMS * 32 + lane);
+  if (tile_len == uint32_t(TILE)) {
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) key[j] = ksrc[wbase + j * 32];
+    if constexpr (VB > 0) {
+#pragma unroll
+      for (int j = 0; j < ITEMS; ++j) val[j] = vsrc[wbase + j * 32];
+    }
+  } else {
+    // past the end: the largest digit, so these items rank after every key
+    // of the tile and are never written
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+      const uint32_t i = wbase + j * 32;
+      key[j] = i < n ? ksrc[i] : ~K(0);
+    }
+    if constexpr (VB > 0) {
+#pragma unroll
+      for (int j = 0; j < ITEMS; ++j) {
+        const uint32_t i = wbase + j * 32;
+        val[j] = i < n ? vsrc[i] : V(0);
+      }
+    }
+  }
+
+  // rank within the warp: peers with the same digit found by match.any; the
+  // warp's running count per digit lives in its private shared counters
+  uint32_t pos[ITEMS];
+  {
+    uint32_t* wh = s_wh + warp * RADIX;
+    const uint32_t lt = lanemask_lt();
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+      const uint32_t d = digit_of(key[j], shift, mask);
+      const uint32_t peers = __match_any_sync(kFull, d);
+      const int leader = 31 - __clz(peers);
+      uint32_t before = 0u;
+      if (lane == leader) before = atomicAdd(&wh[d], uint32_t(__popc(peers)));
+      before = __shfl_sync(kFull, before, leader);
+      pos[j] = before + uint32_t(__popc(peers & lt));
+    }
+  }
+  __syncthreads();
+
+  // per digit: exclusive prefix over warps, tile count, publish the count
+  const bool silent = (int(tile) == knobs.drop_tile) && (pass == knobs.drop_pass);
+  uint32_t my_cnt = 0u;
+  if (tid < RADIX) {
+    uint32_t run = 0u;
+#pragma unroll
+    for (int w = 0; w < WARPS; ++w) {
+      const uint32_t c = s_wh[w * RADIX + tid];
+      s_wh[w * RADIX + tid] = run;
+      run += c;
+    }
+    my_cnt = run;
+    if (!silent)
+      st_relaxed(&status[size_t(tile) * RADIX + tid], (tile == 0u ? kFlagInc : kFlagAgg) | run);
+  }
+  const uint32_t my_start = block_exclusive_scan<THREADS>(my_cnt, s_tot);
+  if (tid < RADIX) {
+    s_cnt[tid] = my_cnt;
+    s_tstart[tid] = my_start;
+  }
+  __syncthreads();
+  for (int i = tid; i < WARPS * RADIX; i += THREADS) s_wh[i] += s_tstart[i & (RADIX - 1)];
+  __syncthreads();
+
+  // local positions; keys into the stage in (digit, input) order
+  K* s_k = reinterpret_cast<K*>(smem + S::STAGE);
+#pragma unroll
+  for (int j = 0; j < ITEMS; ++j) {
+    pos[j] += s_wh[warp * RADIX + digit_of(key[j], shift, mask)];
+    s_k[pos[j]] = key[j];
+  }
+
+  // decoupled look-back: sum the counts of the preceding tiles for my digit
+  if (tid < RADIX) {
+    uint32_t excl = 0u;
+    bool gave_up = false;
+    if (tile > 0u) {
+      int32_t pred = int32_t(tile) - 1;
+      for (;;) {
+        if (pred < 0) {  // only possible if the status words were not cleared
+          report_error(ctrl, kDevIndex, tile);
+          gave_up = true;
+          break;
+        }
+        const uint32_t* p = &status[size_t(pred) * RADIX + tid];
+        uint32_t s = ld_relaxed(p);
+        if ((s & kFlagMask) == 0u) s = wait_status(p, ctrl, knobs.timeout_ns, tile);
+        const uint32_t f = s & kFlagMask;
+        if (f == kFlagErr) {
+          gave_up = true;
+          break;
+        }
+        excl += s & kValueMask;
+        if (f == kFlagInc) break;
+        --pred;
+      }
+      if (!silent)
+        st_relaxed(&status[size_t(tile) * RADIX + tid],
+                   gave_up ? kFlagErr : (kFlagInc | ((excl + my_cnt) & kValueMask)));
+    }
+    if (gave_up) s_misc[1] = 1u;
+    s_gbase[tid] = pass_offsets[tid] + excl - my_start;
+  }
+  __syncthreads();
+  if (s_misc[1]) return;  // the output of this call is void; the host reads ctrl->error
+
+  // scatter: consecutive threads take consecutive stage slots, which map to
+  // consecutive output addresses inside each digit run
+  uint32_t gidx[ITEMS];
+#pragma unroll
+  for (int s = 0; s < ITEMS; ++s) {
+    const uint32_t i = uint32_t(s * THREADS + tid);
+    gidx[s] = 0xffffffffu;
+    if (i < tile_len) {
+      const K k = s_k[i];
+      const uint32_t g = s_gbase[digit_of(k, shift, mask)] + i;
+      if (g < n) {
+        kdst[g] = k;
+        gidx[s] = g;
+      } else {
+        report_error(ctrl, kDevIndex, tile);
+      }
+    }
+  }
+  if constexpr (VB > 0) {
+    __syncthreads();
+    V* s_v = reinterpret_cast<V*>(smem + S::STAGE);
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) s_v[pos[j]] = val[j];
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < ITEMS; ++s) {
+      const uint32_t i = uint32_t(s * THREADS + tid);
+      if (gidx[s] != 0xffffffffu) vdst[gidx[s]] = s_v[i];
+    }
+  }
+}
+
+// ------------------------------------------------------------ small sort
+
+template <class K, int VB, int RADIX_BITS, int THREADS, int ITEMS>
+struct SmallSmem {
+  static constexpr int RADIX = 1 << RADIX_BITS;
+  static constexpr int WARPS = THREADS / 32;
+  static constexpr int TILE = THREADS * ITEMS;
+  static constexpr int ELEM = (int(sizeof(K)) > VB) ? int(sizeof(K)) : VB;
+  static constexpr int WH = 0;                      // u32 [WARPS][RADIX]
+  static constexpr int TOT = WH + WARPS * RADIX * 4; // u32 [32]
+  static constexpr int STAGE = (TOT + 32 * 4 + 15) / 16 * 16;
+  static constexpr int BYTES = STAGE + TILE * ELEM;
+};
+
+// All digit passes of one array of len <= TILE elements inside one CTA.  The
+// input and output may be the same buffers: everything is read before the
+// first write.
+template <class K, int VB, int RADIX_BITS, int THREADS, int ITEMS>
+__device__ __forceinline__ void cta_sort(const K* kin, const ValT<VB>* vin, K* kout,
+                                         ValT<VB>* vout, uint32_t len, int begin_bit,
+                                         int end_bit, unsigned char* smem) {
+  using V = ValT<VB>;
+  using S = SmallSmem<K, VB, RADIX_BITS, THREADS, ITEMS>;
+  constexpr int RADIX = S::RADIX, WARPS = S::WARPS;
+  uint32_t* s_wh = reinterpret_cast<uint32_t*>(smem + S::WH);
+  uint32_t* s_tot = reinterpret_cast<uint32_t*>(smem + S::TOT);
+  K* s_k = reinterpret_cast<K*>(smem + S::STAGE);
+  V* s_v = reinterpret_cast<V*>(smem + S::STAGE);
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t slot0 = uint32_t(warp * ITEMS * 32 + lane);
+  K key[ITEMS];
+  V val[ITEMS];
+#pragma unroll
+  for (int j = 0; j < ITEMS; ++j) {
+    const uint32_t i = slot0 + j * 32;
+    key[j] = i < len ? kin[i] : ~K(0);  // past the end: largest digit in every pass
+    if constexpr (VB > 0) val[j] = i < len ? vin[i] : V(0);
+  }
+  const uint32_t lt = lanemask_lt();
+  for (int lo = begin_bit; lo < end_bit; lo += RADIX_BITS) {
+    const uint32_t shift = uint32_t(lo);
+    const uint32_t mask = (1u << (min(lo + RADIX_BITS, end_bit) - lo)) - 1u;
+    for (int i = tid; i < WARPS * RADIX; i += THREADS) s_wh[i] = 0u;
+    __syncthreads();
+    uint32_t pos[ITEMS];
+    uint32_t* wh = s_wh + warp * RADIX;
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+      const uint32_t d = digit_of(key[j], shift, mask);
+      const uint32_t peers = __match_any_sync(kFull, d);
+      const int leader = 31 - __clz(peers);
+      uint32_t before = 0u;
+      if (lane == leader) before = atomicAdd(&wh[d], uint32_t(__popc(peers)));
+      before = __shfl_sync(kFull, before, leader);
+      pos[j] = before + uint32_t(__popc(peers & lt));
+    }
+    __syncthreads();
+    uint32_t cnt = 0u;
+    if (tid < RADIX) {
+#pragma unroll
+      for (int w = 0; w < WARPS; ++w) {
+        const uint32_t c = s_wh[w * RADIX + tid];
+        s_wh[w * RADIX + tid] = cnt;
+        cnt += c;
+      }
+    }
+    const uint32_t start = block_exclusive_scan<THREADS>(cnt, s_tot);
+    if (tid < RADIX) {
+#pragma unroll
+      for (int w = 0; w < WARPS; ++w) s_wh[w * RADIX + tid] += start;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+      pos[j] += s_wh[warp * RADIX + digit_of(key[j], shift, mask)];
+      s_k[pos[j]] = key[j];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) key[j] = s_k[slot0 + j * 32];
+    if constexpr (VB > 0) {
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < ITEMS; ++j) s_v[pos[j]] = val[j];
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < ITEMS; ++j) val[j] = s_v[slot0 + j * 32];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int j = 0; j < ITEMS; ++j) {
+    const uint32_t i = slot0 + j * 32;
+    if (i < len) {
+      kout[i] = key[j];
+      if constexpr (VB > 0) vout[i] = val[j];
+    }
+  }
+}
+
+template <class K, int VB, int RADIX_BITS, int THREADS, int ITEMS>
+__global__ void __launch_bounds__(THREADS, 1)
+    k_small_sort(K* keys, ValT<VB>* vals, uint32_t n, int begin_bit, int end_bit) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  cta_sort<K, VB, RADIX_BITS, THREADS, ITEMS>(keys, vals, keys, vals, n, begin_bit, end_bit,
+                                              smem);
+}
+
+}  // namespace rs

@@ -1,0 +1,144 @@
+// Host launchers of the sort variants (one instantiation per compiled tile
+// shape).  Each launcher enqueues a complete sort on the caller's stream:
+//   memset(ctrl + counts) -> k_upsweep -> k_onesweep x passes
+// or, for arrays that fit one tile, a single k_small_sort.
+#pragma once
+
+#include <algorithm>
+
+#include "rs_host.h"
+#include "rs_kernels.cuh"
+
+namespace rs {
+
+template <class K, int VB, int R, int THREADS, int ITEMS, int MINB>
+struct OnesweepSort {
+  static constexpr int RADIX = 1 << R;
+  static constexpr int TILE = THREADS * ITEMS;
+  static constexpr int UP_THREADS = 1024;
+  static constexpr int MAXP = (8 * int(sizeof(K)) + R - 1) / R;
+  using S = OnesweepSmem<K, VB, R, THREADS, ITEMS>;
+
+  static size_t tiles(uint32_t n) { return (size_t(n) + TILE - 1) / TILE; }
+
+  static size_t workspace(uint32_t n, int passes) {
+    return onesweep_layout(passes, R, tiles(n)).total;
+  }
+
+  static cudaError_t upsweep(const SortArgs& a, int passes, const Layout& L, bool clear_status) {
+    char* ws = static_cast<char*>(a.ws);
+    Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws);
+    cudaError_t e = cudaMemsetAsync(ws, 0, L.memset_bytes, a.stream);
+    if (e != cudaSuccess) return e;
+    const void* f = reinterpret_cast<const void*>(&k_upsweep<K, R, UP_THREADS, MAXP>);
+    const int max_smem = MAXP * (RADIX / 2) * 32 * 4;
+    const int occ = prepare_kernel(f, UP_THREADS, max_smem);
+    if (occ <= 0) return cudaErrorInvalidConfiguration;
+    const int smem = passes * (RADIX / 2) * 32 * 4;
+    constexpr uint32_t per_cta = UP_THREADS * (16 / sizeof(K)) * 4;
+    const uint32_t want = (a.n + per_cta - 1) / per_cta;
+    const uint32_t grid =
+        std::max(1u, std::min(uint32_t(device_info().sms * occ), want));
+    const uint64_t zero_vec4 = clear_status ? L.status_bytes / 16 : 0;
+    prof_before(a.stream);
+    k_upsweep<K, R, UP_THREADS, MAXP><<<grid, UP_THREADS, smem, a.stream>>>(
+        static_cast<const K*>(a.keys), a.n, a.begin_bit, a.end_bit, passes,
+        reinterpret_cast<uint32_t*>(ws + L.counts), reinterpret_cast<uint32_t*>(ws + L.offsets),
+        ctrl, reinterpret_cast<uint4*>(ws + L.status), zero_vec4);
+    e = cudaGetLastError();
+    prof_after(a.stream, 0, double(a.n) * sizeof(K));
+    return e;
+  }
+
+  static cudaError_t run(const SortArgs& a, int* in_alt) {
+    const int passes = num_passes(a.begin_bit, a.end_bit, R);
+    *in_alt = passes & 1;
+    const size_t nt = tiles(a.n);
+    const Layout L = onesweep_layout(passes, R, nt);
+    cudaError_t e = upsweep(a, passes, L, true);
+    if (e != cudaSuccess) return e;
+    char* ws = static_cast<char*>(a.ws);
+    Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws);
+    const int slot = prof_note_mask(a.stream, &ctrl->exec_mask);
+    using V = ValT<VB>;
+    auto kern = &k_onesweep<K, VB, R, THREADS, ITEMS, MINB>;
+    if (prepare_kernel(reinterpret_cast<const void*>(kern), THREADS, S::BYTES) <= 0)
+      return cudaErrorInvalidConfiguration;
+    const double bytes = 2.0 * double(a.n) * double(sizeof(K) + VB);
+    for (int p = 0; p < passes; ++p) {
+      const int lo = a.begin_bit + p * R;
+      const int width = std::min(R, a.end_bit - lo);
+      const uint32_t mask = (1u << width) - 1u;
+      prof_before(a.stream);
+      kern<<<unsigned(nt), THREADS, S::BYTES, a.stream>>>(
+          static_cast<K*>(a.keys), static_cast<K*>(a.keys_alt), static_cast<V*>(a.vals),
+          static_cast<V*>(a.vals_alt), a.n, p, uint32_t(lo), mask,
+          reinterpret_cast<const uint32_t*>(ws + L.offsets) + size_t(p) * RADIX,
+          reinterpret_cast<uint32_t*>(ws + L.status) + size_t(p) * nt * RADIX, ctrl, a.knobs);
+      e = cudaGetLastError();
+      prof_after(a.stream, 1, bytes, slot, p);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
+
+  static cudaError_t count(const SortArgs& a) {
+    const int passes = num_passes(a.begin_bit, a.end_bit, R);
+    const Layout L = onesweep_layout(passes, R, tiles(a.n));
+    return upsweep(a, passes, L, false);
+  }
+
+  static Variant describe() {
+    Variant v{};
+    v.key_bytes = int(sizeof(K));
+    v.val_bytes = VB;
+    v.kind = kOnesweep;
+    v.radix_bits = R;
+    v.threads = THREADS;
+    v.items = ITEMS;
+    v.max_n = (1u << 30) - 1u;
+    v.workspace = &workspace;
+    v.run = &run;
+    v.count = &count;
+    return v;
+  }
+};
+
+template <class K, int VB, int R, int THREADS, int ITEMS>
+struct SmallSort {
+  static constexpr int TILE = THREADS * ITEMS;
+  using S = SmallSmem<K, VB, R, THREADS, ITEMS>;
+
+  static size_t workspace(uint32_t, int) { return 0; }
+
+  static cudaError_t run(const SortArgs& a, int* in_alt) {
+    using V = ValT<VB>;
+    *in_alt = 0;  // sorted in place
+    auto kern = &k_small_sort<K, VB, R, THREADS, ITEMS>;
+    if (prepare_kernel(reinterpret_cast<const void*>(kern), THREADS, S::BYTES) <= 0)
+      return cudaErrorInvalidConfiguration;
+    prof_before(a.stream);
+    kern<<<1, THREADS, S::BYTES, a.stream>>>(static_cast<K*>(a.keys), static_cast<V*>(a.vals),
+                                             a.n, a.begin_bit, a.end_bit);
+    const cudaError_t e = cudaGetLastError();
+    prof_after(a.stream, 2, 2.0 * double(a.n) * double(sizeof(K) + VB));
+    return e;
+  }
+
+  static Variant describe() {
+    Variant v{};
+    v.key_bytes = int(sizeof(K));
+    v.val_bytes = VB;
+    v.kind = kSmall;
+    v.radix_bits = R;
+    v.threads = THREADS;
+    v.items = ITEMS;
+    v.max_n = TILE;
+    v.workspace = &workspace;
+    v.run = &run;
+    v.count = nullptr;
+    return v;
+  }
+};
+
+}  // namespace rs

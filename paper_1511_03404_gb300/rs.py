@@ -1,0 +1,279 @@
+"""Python binding of the rs C ABI (include/rs.h): ctypes, argument marshalling only.
+
+Every function named ``rs_*`` here calls the C entry point of the same name
+in ``_build/librs.so`` with plain integers (device pointers, sizes, a
+``cudaStream_t`` handle) and returns what it returns; every step of the sort
+runs in the library's CUDA kernels.  There is no CPU fallback: if the library
+cannot be built or loaded, loading raises.
+
+``sort()`` and ``segmented_sort()`` at the bottom are conveniences over torch
+tensors: torch only provides the device memory and the stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import _build
+
+RS_OK = 0
+RS_ERR_INVALID = 1
+RS_ERR_NOMEM = 2
+RS_ERR_CUDA = 3
+RS_ERR_TIMEOUT = 4
+RS_ERR_BUSY = 5
+RS_ERR_WORKSPACE = 6
+RS_ERR_DEVICE = 7
+RS_ERR_CANCELLED = 8
+RS_ERR_NOT_FOUND = 9
+RS_MAX_N = (1 << 30) - 1
+
+RS_KERNEL_UPSWEEP, RS_KERNEL_ONESWEEP, RS_KERNEL_SMALL, RS_KERNEL_SEGMENTED = range(4)
+RS_KERNEL_KINDS = 4
+KERNEL_NAMES = ("upsweep", "onesweep", "small", "segmented")
+
+RS_DEBUG_TIMEOUT_NS, RS_DEBUG_DROP_PUBLISH_TILE, RS_DEBUG_DROP_PUBLISH_PASS = range(3)
+
+
+class RsError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)}")
+
+
+class rs_config(ctypes.Structure):
+    _fields_ = [("radix_bits", ctypes.c_int), ("variant", ctypes.c_int)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+_vp, _sz, _i, _u32p = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p
+_SIGS = {
+    "rs_status_string": ([_i], ctypes.c_char_p),
+    "rs_version": ([], ctypes.c_char_p),
+    "rs_num_variants": ([_i, _i], _i),
+    "rs_variant_info": ([_i, _i, _i, _vp, _vp, _vp, _vp, _vp], _i),
+    "rs_workspace_bytes": ([_i, _i, _sz, _i, _i, _vp, _vp], _i),
+    "rs_sort_keys_u32": ([_vp, _vp, _sz, _i, _i, _vp, _sz, _vp, _vp], _i),
+    "rs_sort_keys_u64": ([_vp, _vp, _sz, _i, _i, _vp, _sz, _vp, _vp], _i),
+    "rs_sort_pairs_u32": ([_vp, _vp, _vp, _vp, _sz, _i, _i, _vp, _sz, _vp, _vp], _i),
+    "rs_sort_pairs_u64": ([_vp, _vp, _vp, _vp, _sz, _i, _i, _vp, _sz, _vp, _vp], _i),
+    "rs_sort": ([_i, _i, _vp, _vp, _vp, _vp, _sz, _i, _i, _vp, _vp, _sz, _vp, _vp], _i),
+    "rs_digit_counts": ([_i, _vp, _sz, _i, _i, _i, _vp, _vp, _vp, _vp, _sz, _vp], _i),
+    "rs_workspace_status": ([_vp, _vp, _vp], _i),
+    "rs_profile_begin": ([_i], _i),
+    "rs_profile_end": ([_vp, _vp, _vp], _i),
+    "rs_debug_set": ([_i, ctypes.c_longlong], _i),
+}
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def load():
+    """Build (if needed) and load librs.so; raises if that is impossible."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            lib = ctypes.CDLL(path, mode=ctypes.RTLD_GLOBAL)
+            for name, (args, res) in _SIGS.items():
+                if not hasattr(lib, name):
+                    continue  # declared later in the header than this build
+                fn = getattr(lib, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = lib
+    return _lib
+
+
+def declared_symbols() -> list[str]:
+    return list(_SIGS)
+
+
+def status_string(status: int) -> str:
+    return load().rs_status_string(status).decode()
+
+
+def check(status: int, what: str = "rs") -> None:
+    if status != RS_OK:
+        raise RsError(status, what)
+
+
+def _out_int():
+    return ctypes.c_int(0)
+
+
+# ------------------------------------------------------------------ C ABI
+# Same names and arguments as include/rs.h; pointers are Python ints.
+
+def rs_version() -> str:
+    return load().rs_version().decode()
+
+
+def rs_num_variants(key_bytes: int, val_bytes: int) -> int:
+    return load().rs_num_variants(key_bytes, val_bytes)
+
+
+def rs_variant_info(key_bytes: int, val_bytes: int, index: int):
+    r, t, it, k = (ctypes.c_int() for _ in range(4))
+    mx = ctypes.c_size_t()
+    st = load().rs_variant_info(key_bytes, val_bytes, index, ctypes.byref(r), ctypes.byref(t),
+                                ctypes.byref(it), ctypes.byref(k), ctypes.byref(mx))
+    check(st, "rs_variant_info")
+    return {"radix_bits": r.value, "threads": t.value, "items": it.value, "kind": k.value,
+            "max_n": mx.value}
+
+
+def _cfg(radix_bits=0, variant=-1):
+    if radix_bits == 0 and variant < 0:
+        return None
+    return ctypes.byref(rs_config(radix_bits, variant))
+
+
+def rs_workspace_bytes(key_bytes, val_bytes, n, begin_bit, end_bit, radix_bits=0, variant=-1):
+    out = ctypes.c_size_t()
+    st = load().rs_workspace_bytes(key_bytes, val_bytes, n, begin_bit, end_bit,
+                                   _cfg(radix_bits, variant), ctypes.byref(out))
+    return st, out.value
+
+
+def rs_sort_keys_u32(keys, keys_alt, n, begin_bit, end_bit, ws, ws_bytes, stream):
+    r = _out_int()
+    st = load().rs_sort_keys_u32(keys, keys_alt, n, begin_bit, end_bit, ws, ws_bytes, stream,
+                                 ctypes.byref(r))
+    return st, r.value
+
+
+def rs_sort_keys_u64(keys, keys_alt, n, begin_bit, end_bit, ws, ws_bytes, stream):
+    r = _out_int()
+    st = load().rs_sort_keys_u64(keys, keys_alt, n, begin_bit, end_bit, ws, ws_bytes, stream,
+                                 ctypes.byref(r))
+    return st, r.value
+
+
+def rs_sort_pairs_u32(keys, vals, keys_alt, vals_alt, n, begin_bit, end_bit, ws, ws_bytes, stream):
+    r = _out_int()
+    st = load().rs_sort_pairs_u32(keys, vals, keys_alt, vals_alt, n, begin_bit, end_bit, ws,
+                                  ws_bytes, stream, ctypes.byref(r))
+    return st, r.value
+
+
+def rs_sort_pairs_u64(keys, vals, keys_alt, vals_alt, n, begin_bit, end_bit, ws, ws_bytes, stream):
+    r = _out_int()
+    st = load().rs_sort_pairs_u64(keys, vals, keys_alt, vals_alt, n, begin_bit, end_bit, ws,
+                                  ws_bytes, stream, ctypes.byref(r))
+    return st, r.value
+
+
+def rs_sort(key_bytes, val_bytes, keys, vals, keys_alt, vals_alt, n, begin_bit, end_bit, ws,
+            ws_bytes, stream, radix_bits=0, variant=-1):
+    r = _out_int()
+    st = load().rs_sort(key_bytes, val_bytes, keys, vals, keys_alt, vals_alt, n, begin_bit,
+                        end_bit, _cfg(radix_bits, variant), ws, ws_bytes, stream,
+                        ctypes.byref(r))
+    return st, r.value
+
+
+def rs_digit_counts(key_bytes, keys, n, begin_bit, end_bit, radix_bits, d_counts, d_offsets,
+                    d_exec_mask, ws, ws_bytes, stream):
+    return load().rs_digit_counts(key_bytes, keys, n, begin_bit, end_bit, radix_bits, d_counts,
+                                  d_offsets, d_exec_mask, ws, ws_bytes, stream)
+
+
+def rs_workspace_status(ws, stream):
+    info = ctypes.c_uint32()
+    st = load().rs_workspace_status(ws, stream, ctypes.byref(info))
+    return st, info.value
+
+
+def rs_profile_begin(capacity: int) -> int:
+    return load().rs_profile_begin(capacity)
+
+
+def rs_profile_end():
+    launches = (ctypes.c_int * RS_KERNEL_KINDS)()
+    ms = (ctypes.c_double * RS_KERNEL_KINDS)()
+    by = (ctypes.c_double * RS_KERNEL_KINDS)()
+    st = load().rs_profile_end(launches, ms, by)
+    return st, {KERNEL_NAMES[k]: {"launches": launches[k], "ms": ms[k], "bytes": by[k]}
+                for k in range(RS_KERNEL_KINDS)}
+
+
+def rs_debug_set(knob: int, value: int) -> int:
+    return load().rs_debug_set(knob, value)
+
+
+# ------------------------------------------------------- torch conveniences
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_handle(stream=None) -> int:
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+_KEY_BYTES = {"uint32": 4, "int32": 4, "uint64": 8, "int64": 8}
+
+
+def _key_bytes(t) -> int:
+    name = str(t.dtype).replace("torch.", "")
+    if name not in _KEY_BYTES:
+        raise TypeError(f"keys must be a 32- or 64-bit integer tensor, got {t.dtype}")
+    return _KEY_BYTES[name]
+
+
+def workspace(key_bytes, val_bytes, n, begin_bit=0, end_bit=None, radix_bits=0, variant=-1,
+              device=None):
+    """A torch uint8 device tensor large enough for one sort."""
+    torch = _torch()
+    end_bit = 8 * key_bytes if end_bit is None else end_bit
+    st, nbytes = rs_workspace_bytes(key_bytes, val_bytes, n, begin_bit, end_bit, radix_bits,
+                                    variant)
+    check(st, "rs_workspace_bytes")
+    return torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device or "cuda")
+
+
+def sort(keys, vals=None, begin_bit=0, end_bit=None, radix_bits=0, variant=-1, stream=None,
+         ws=None, alt=None):
+    """Sort contiguous device tensors in place (ascending unsigned, stable).
+
+    ``keys`` (and ``vals``, same dtype width) are overwritten with the sorted
+    sequence; signed dtypes are sorted as their unsigned bit patterns.
+    Returns ``(keys, vals)``.
+    """
+    torch = _torch()
+    if not keys.is_cuda or not keys.is_contiguous():
+        raise ValueError("keys must be a contiguous CUDA tensor")
+    kb = _key_bytes(keys)
+    vb = 0
+    if vals is not None:
+        vb = _key_bytes(vals)
+        if vb != kb or vals.numel() != keys.numel() or not vals.is_contiguous():
+            raise ValueError("vals must match the keys' width and length")
+    n = keys.numel()
+    end_bit = 8 * kb if end_bit is None else end_bit
+    if ws is None:
+        ws = workspace(kb, vb, n, begin_bit, end_bit, radix_bits, variant, keys.device)
+    if alt is None:
+        ka = torch.empty_like(keys)
+        va = torch.empty_like(vals) if vals is not None else None
+    else:
+        ka, va = alt
+    st, in_alt = rs_sort(kb, vb, keys.data_ptr(), vals.data_ptr() if vals is not None else None,
+                         ka.data_ptr(), va.data_ptr() if va is not None else None, n, begin_bit,
+                         end_bit, ws.data_ptr(), ws.numel(), _stream_handle(stream), radix_bits,
+                         variant)
+    check(st, "rs_sort")
+    if in_alt:
+        keys.copy_(ka)
+        if vals is not None:
+            vals.copy_(va)
+    return keys, vals

@@ -1,0 +1,103 @@
+"""The C-ABI library loads on a machine without a GPU, exports every entry
+point include/*.h declares, and rejects bad arguments on the host before it
+touches CUDA.  No compute call is made here."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from paper_1511_03404_gb300 import _build, rs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w\s\*]*?\b(rs_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol():
+    lib = rs.load()
+    names = declared_functions()
+    assert len(names) >= 15
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    # the binding covers the same names
+    assert not [n for n in names if not hasattr(rs, n) and n not in ("rs_status_string",)]
+
+
+def test_built_for_sm103a_only():
+    assert _build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+    assert os.path.exists(_build.LIB_PATH)
+
+
+def test_status_strings_and_version():
+    assert rs.status_string(rs.RS_OK) == "RS_OK"
+    assert "TIMEOUT" in rs.status_string(rs.RS_ERR_TIMEOUT)
+    assert re.match(r"\d+\.\d+\.\d+", rs.rs_version())
+
+
+def test_variants_described():
+    for kb, vb in ((4, 0), (4, 4), (8, 0), (8, 8)):
+        n = rs.rs_num_variants(kb, vb)
+        assert n >= 2
+        kinds = set()
+        for i in range(n):
+            info = rs.rs_variant_info(kb, vb, i)
+            assert 4 <= info["radix_bits"] <= 8 and info["threads"] % 32 == 0
+            kinds.add(info["kind"])
+        assert kinds == {0, 1}
+    assert rs.rs_num_variants(4, 8) == 0
+    with pytest.raises(rs.RsError):
+        rs.rs_variant_info(4, 4, 99)
+
+
+def test_workspace_sizes():
+    st, b = rs.rs_workspace_bytes(4, 4, 0, 0, 32)
+    assert st == rs.RS_OK and b == 0
+    st, b = rs.rs_workspace_bytes(4, 4, 1000, 0, 32)  # one-CTA path: no workspace
+    assert st == rs.RS_OK and b == 0
+    st, b1 = rs.rs_workspace_bytes(4, 4, 2**26, 0, 32)
+    assert st == rs.RS_OK
+    # onesweep: 256 B control + counts + offsets + look-back words of every pass
+    info = rs.rs_variant_info(4, 4, 0)
+    tiles = -(-2**26 // (info["threads"] * info["items"]))
+    assert b1 >= 4 * tiles * 256 * 4 + 2 * 4 * 256 * 4
+    assert b1 < 4 * tiles * 256 * 4 + 16384
+    st, b2 = rs.rs_workspace_bytes(8, 0, 2**26, 0, 64)
+    assert st == rs.RS_OK and b2 > b1
+    assert rs.rs_workspace_bytes(4, 4, rs.RS_MAX_N + 1, 0, 32)[0] == rs.RS_ERR_INVALID
+    assert rs.rs_workspace_bytes(4, 4, 100, 0, 33)[0] == rs.RS_ERR_INVALID
+    assert rs.rs_workspace_bytes(4, 8, 100, 0, 32)[0] == rs.RS_ERR_INVALID
+
+
+def test_host_argument_checks_without_gpu():
+    fake = 1 << 40  # never dereferenced: every call below fails its host checks
+    # wrong type combination
+    assert rs.rs_sort(4, 8, fake, fake + 4096, fake + 8192, fake + 12288, 100, 0, 32, None, 0,
+                      None)[0] == rs.RS_ERR_INVALID
+    # values given for a keys-only sort
+    assert rs.rs_sort(4, 0, fake, fake + 4096, fake + 8192, None, 100, 0, 32, None, 0,
+                      None)[0] == rs.RS_ERR_INVALID
+    # bit range
+    assert rs.rs_sort_keys_u32(fake, fake + 4096, 100, 5, 4, None, 0, None)[0] == rs.RS_ERR_INVALID
+    assert rs.rs_sort_keys_u64(fake, fake + 4096, 100, 0, 65, None, 0, None)[0] == rs.RS_ERR_INVALID
+    # too many elements
+    assert rs.rs_sort_keys_u32(fake, fake + 4096, rs.RS_MAX_N + 1, 0, 32, None, 0,
+                               None)[0] == rs.RS_ERR_INVALID
+    # missing workspace for a multi-CTA sort
+    assert rs.rs_sort_keys_u32(fake, fake + 2**30, 2**20, 0, 32, None, 0,
+                               None)[0] == rs.RS_ERR_WORKSPACE
+    # trivially sorted inputs return at once, in place
+    assert rs.rs_sort_keys_u32(fake, fake + 4096, 1, 0, 32, None, 0, None) == (rs.RS_OK, 0)
+    assert rs.rs_sort_pairs_u64(fake, fake + 8, fake + 16, fake + 24, 500, 9, 9, None, 0,
+                                None) == (rs.RS_OK, 0)
+    assert rs.rs_debug_set(99, 1) == rs.RS_ERR_INVALID
+    assert rs.rs_profile_end()[0] == rs.RS_ERR_INVALID

@@ -36,6 +36,8 @@
  *     only be seen on the device (a bounded wait that ran out, an index
  *     check that failed) are recorded in a status word inside the workspace;
  *     read it with rs_workspace_status() after the stream's work is done.
+ *     Every sort given a workspace of at least 256 bytes resets that status
+ *     word, even on paths that need no other workspace.
  *     The library never aborts, traps or hangs: every device-side wait is
  *     bounded in time.
  *   - Limits: n <= RS_MAX_N.  0 <= begin_bit <= end_bit <= key bits.
@@ -169,6 +171,31 @@ rs_status rs_digit_counts(int key_bytes, const void* keys, size_t n, int begin_b
  * or pass the device reported.
  */
 rs_status rs_workspace_status(const void* ws, rs_stream_t stream, uint32_t* info);
+
+/*
+ * Batched segmented sort of 32-bit key-value pairs: the sort of Sec. 2.6
+ * applied independently to every segment of one array, all segments in one
+ * persistent kernel launch (after a one-CTA planning launch).
+ *   keys, vals, keys_alt, vals_alt  [n] u32 device buffers as for rs_sort_pairs_u32
+ *   d_offsets  [n_seg + 1] u64 device: segment s is [d_offsets[s], d_offsets[s+1]);
+ *              d_offsets[0] = 0, non-decreasing, d_offsets[n_seg] = n, and no
+ *              segment longer than RS_MAX_N.  Offsets that break these rules are
+ *              reported by rs_workspace_status() as RS_ERR_INVALID and no
+ *              element is written.
+ * Every segment is sorted over [begin_bit, end_bit), stable.  *result_in_alt
+ * (host) names the buffer pair that holds every sorted segment; it depends
+ * only on the bit range: 1 when ceil((end_bit - begin_bit) / 8) is odd.
+ * ws: at least rs_segmented_workspace_bytes(n, n_seg, ...) bytes, 256-aligned.
+ * The host reads nothing from the device: the plan is made on the GPU.
+ */
+rs_status rs_segmented_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
+                                  uint32_t* vals_alt, size_t n, const uint64_t* d_offsets,
+                                  size_t n_seg, int begin_bit, int end_bit, void* ws,
+                                  size_t ws_bytes, rs_stream_t stream, int* result_in_alt);
+
+/* Workspace bytes rs_segmented_sort_pairs needs for n elements in n_seg segments. */
+rs_status rs_segmented_workspace_bytes(size_t n, size_t n_seg, int begin_bit, int end_bit,
+                                       size_t* bytes);
 
 /* ---- per-kernel timing (CUDA events recorded on the sort's stream) ---- */
 

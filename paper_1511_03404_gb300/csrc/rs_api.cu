@@ -75,7 +75,7 @@ static std::atomic<long long> g_timeout_ns{1000000000LL};
 static std::atomic<long long> g_drop_tile{-1};
 static std::atomic<long long> g_drop_pass{-1};
 
-static Knobs current_knobs() {
+Knobs knobs_now() {
   Knobs k;
   k.timeout_ns = uint64_t(g_timeout_ns.load());
   k.drop_tile = int32_t(g_drop_tile.load());
@@ -229,9 +229,15 @@ rs_status rs_sort(int key_bytes, int val_bytes, void* keys, void* vals, void* ke
   if (!result_in_alt || !valid_types(key_bytes, val_bytes)) return RS_ERR_INVALID;
   if (n > RS_MAX_N || begin_bit < 0 || begin_bit > end_bit || end_bit > 8 * key_bytes)
     return RS_ERR_INVALID;
-  if ((val_bytes == 0) != (vals == nullptr && vals_alt == nullptr)) return RS_ERR_INVALID;
   *result_in_alt = 0;
-  if (n <= 1 || begin_bit == end_bit) return RS_OK;  // already sorted, nothing moves
+  if (n <= 1 || begin_bit == end_bit) {  // already sorted, nothing moves
+    if (ws && ws_bytes >= sizeof(Ctrl) &&
+        cudaMemsetAsync(ws, 0, 2 * sizeof(uint32_t), reinterpret_cast<cudaStream_t>(stream)) !=
+            cudaSuccess)
+      return RS_ERR_CUDA;
+    return RS_OK;
+  }
+  if ((val_bytes == 0) != (vals == nullptr && vals_alt == nullptr)) return RS_ERR_INVALID;
   if (!keys || !keys_alt || keys == keys_alt) return RS_ERR_INVALID;
   if (!aligned(keys, key_bytes) || !aligned(keys_alt, key_bytes)) return RS_ERR_INVALID;
   if (val_bytes) {
@@ -244,7 +250,7 @@ rs_status rs_sort(int key_bytes, int val_bytes, void* keys, void* vals, void* ke
   const size_t need = v->workspace(uint32_t(n), passes);
   if (need > 0 && (!ws || ws_bytes < need || !aligned(ws, 256))) return RS_ERR_WORKSPACE;
   SortArgs a{keys, vals, keys_alt, vals_alt, uint32_t(n), begin_bit, end_bit, ws, ws_bytes,
-             reinterpret_cast<cudaStream_t>(stream), current_knobs()};
+             reinterpret_cast<cudaStream_t>(stream), knobs_now()};
   int in_alt = 0;
   const cudaError_t e = v->run(a, &in_alt);
   if (e != cudaSuccess) return RS_ERR_CUDA;
@@ -299,7 +305,7 @@ rs_status rs_digit_counts(int key_bytes, const void* keys, size_t n, int begin_b
   if (!ws || ws_bytes < L.status || !aligned(ws, 256)) return RS_ERR_WORKSPACE;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   SortArgs a{const_cast<void*>(keys), nullptr, nullptr, nullptr, uint32_t(n), begin_bit,
-             end_bit, ws, ws_bytes, s, current_knobs()};
+             end_bit, ws, ws_bytes, s, knobs_now()};
   if (v->count(a) != cudaSuccess) return RS_ERR_CUDA;
   const size_t table = size_t(passes) << radix_bits;
   char* w = static_cast<char*>(ws);
@@ -323,6 +329,7 @@ rs_status rs_workspace_status(const void* ws, rs_stream_t stream, uint32_t* info
   switch (head[0]) {
     case kDevOk: return RS_OK;
     case kDevTimeout: return RS_ERR_TIMEOUT;
+    case 1u: return RS_ERR_INVALID;  // e.g. segment offsets that do not describe the array
     default: return RS_ERR_DEVICE;
   }
 }

@@ -65,6 +65,9 @@ void prof_before(cudaStream_t s);
 int prof_note_mask(cudaStream_t s, const uint32_t* d_exec_mask);
 void prof_after(cudaStream_t s, int kind, double bytes, int mask_slot = -1, int pass = -1);
 
+// Current fault-injection / wait-limit settings (rs_debug_set).
+Knobs knobs_now();
+
 inline int num_passes(int begin_bit, int end_bit, int radix_bits) {
   return (end_bit - begin_bit + radix_bits - 1) / radix_bits;
 }

@@ -272,46 +272,51 @@ struct OnesweepSmem {
   static constexpr int BYTES = STAGE + TILE * ELEM;
 };
 
-// One digit pass over one tile per CTA.  The grid has one CTA per tile; tile
-// ids come from an atomic counter so that a tile's predecessors have always
-// started before it (forward progress of the look-back).
-template <class K, int VB, int RADIX_BITS, int THREADS, int ITEMS, int MINB>
-__global__ void __launch_bounds__(THREADS, MINB)
-    k_onesweep(K* __restrict__ k0, K* __restrict__ k1, ValT<VB>* __restrict__ v0,
-               ValT<VB>* __restrict__ v1, uint32_t n, int pass, uint32_t shift, uint32_t mask,
-               const uint32_t* __restrict__ pass_offsets, uint32_t* __restrict__ status,
-               Ctrl* __restrict__ ctrl, Knobs knobs) {
+// Operands of one tile of one digit pass over one array (or one segment).
+template <class K, int VB>
+struct TileArgs {
+  const K* ksrc;
+  K* kdst;
+  const ValT<VB>* vsrc;
+  ValT<VB>* vdst;
+  uint32_t n;                   // elements of the array / segment
+  uint32_t tile;                // tile index inside the array / segment
+  uint32_t shift, mask;         // digit of this pass: (key >> shift) & mask
+  const uint32_t* pass_offsets; // [RADIX] global digit offsets of this pass
+  uint32_t* status;             // [tiles][RADIX] look-back words of this array and pass
+  bool silent;                  // test-only: publish nothing for this tile
+};
+
+template <bool CG, class T>
+__device__ __forceinline__ T load_elem(const T* p) {
+  if constexpr (CG) return __ldcg(p);  // L2 only: written by other CTAs of this kernel
+  else return *p;
+}
+
+// One tile of one counting-sort pass (Sec. 2.6): rank, publish, look back,
+// stable scatter.  Every thread of the CTA calls it; it starts by clearing
+// the warp counters.  Returns false (CTA-uniform) when a bounded wait gave
+// up, in which case nothing of this tile was written.
+template <class K, int VB, int RADIX_BITS, int THREADS, int ITEMS, bool CG>
+__device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ctrl,
+                                              uint64_t timeout_ns, unsigned char* smem) {
   using V = ValT<VB>;
   using S = OnesweepSmem<K, VB, RADIX_BITS, THREADS, ITEMS>;
   constexpr int RADIX = S::RADIX, WARPS = S::WARPS, TILE = S::TILE;
   static_assert(RADIX <= THREADS, "one thread per digit");
-
-  extern __shared__ __align__(16) unsigned char smem[];
   uint32_t* s_wh = reinterpret_cast<uint32_t*>(smem + S::WH);
   uint32_t* s_cnt = reinterpret_cast<uint32_t*>(smem + S::CNT);
   uint32_t* s_tstart = reinterpret_cast<uint32_t*>(smem + S::TSTART);
   uint32_t* s_gbase = reinterpret_cast<uint32_t*>(smem + S::GBASE);
   uint32_t* s_tot = reinterpret_cast<uint32_t*>(smem + S::TOT);
   uint32_t* s_misc = reinterpret_cast<uint32_t*>(smem + S::MISC);
-
-  const uint32_t exec = ctrl->exec_mask;
-  if (!((exec >> pass) & 1u)) return;  // every key has the same digit: nothing moves
-  const bool from_alt = (__popc(exec & ((1u << pass) - 1u)) & 1) != 0;
-  const K* __restrict__ ksrc = from_alt ? k1 : k0;
-  K* __restrict__ kdst = from_alt ? k0 : k1;
-  const V* __restrict__ vsrc = from_alt ? v1 : v0;
-  V* __restrict__ vdst = from_alt ? v0 : v1;
-
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) {
-    s_misc[0] = atomicAdd(&ctrl->tile_counter[pass], 1u);
-    s_misc[1] = 0u;
-    s_misc[2] = ld_relaxed(&ctrl->error);  // an earlier pass of this call gave up
-  }
+
   for (int i = tid; i < WARPS * RADIX; i += THREADS) s_wh[i] = 0u;
+  if (tid == 0) s_misc[1] = 0u;
   __syncthreads();
-  if (s_misc[2] != 0u) return;  // CTA-uniform
-  const uint32_t tile = s_misc[0];
+
+  const uint32_t tile = t.tile, n = t.n;
   const uint32_t tile_base = tile * uint32_t(TILE);
   const uint32_t tile_len = min(uint32_t(TILE), n - tile_base);
 
@@ -322,10 +327,10 @@ __global__ void __launch_bounds__(THREADS, MINB)
   const uint32_t wbase = tile_base + uint32_t(warp * ITEMS * 32 + lane);
   if (tile_len == uint32_t(TILE)) {
 #pragma unroll
-    for (int j = 0; j < ITEMS; ++j) key[j] = ksrc[wbase + j * 32];
+    for (int j = 0; j < ITEMS; ++j) key[j] = load_elem<CG>(t.ksrc + wbase + j * 32);
     if constexpr (VB > 0) {
 #pragma unroll
-      for (int j = 0; j < ITEMS; ++j) val[j] = vsrc[wbase + j * 32];
+      for (int j = 0; j < ITEMS; ++j) val[j] = load_elem<CG>(t.vsrc + wbase + j * 32);
     }
   } else {
     // past the end: the largest digit, so these items rank after every key
@@ -333,13 +338,13 @@ __global__ void __launch_bounds__(THREADS, MINB)
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
       const uint32_t i = wbase + j * 32;
-      key[j] = i < n ? ksrc[i] : ~K(0);
+      key[j] = i < n ? load_elem<CG>(t.ksrc + i) : ~K(0);
     }
     if constexpr (VB > 0) {
 #pragma unroll
       for (int j = 0; j < ITEMS; ++j) {
         const uint32_t i = wbase + j * 32;
-        val[j] = i < n ? vsrc[i] : V(0);
+        val[j] = i < n ? load_elem<CG>(t.vsrc + i) : V(0);
       }
     }
   }
@@ -352,7 +357,7 @@ __global__ void __launch_bounds__(THREADS, MINB)
     const uint32_t lt = lanemask_lt();
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
-      const uint32_t d = digit_of(key[j], shift, mask);
+      const uint32_t d = digit_of(key[j], t.shift, t.mask);
       const uint32_t peers = __match_any_sync(kFull, d);
       const int leader = 31 - __clz(peers);
       uint32_t before = 0u;
@@ -364,7 +369,6 @@ __global__ void __launch_bounds__(THREADS, MINB)
   __syncthreads();
 
   // per digit: exclusive prefix over warps, tile count, publish the count
-  const bool silent = (int(tile) == knobs.drop_tile) && (pass == knobs.drop_pass);
   uint32_t my_cnt = 0u;
   if (tid < RADIX) {
     uint32_t run = 0u;
@@ -375,8 +379,8 @@ __global__ void __launch_bounds__(THREADS, MINB)
       run += c;
     }
     my_cnt = run;
-    if (!silent)
-      st_relaxed(&status[size_t(tile) * RADIX + tid], (tile == 0u ? kFlagInc : kFlagAgg) | run);
+    if (!t.silent)
+      st_relaxed(&t.status[size_t(tile) * RADIX + tid], (tile == 0u ? kFlagInc : kFlagAgg) | run);
   }
   const uint32_t my_start = block_exclusive_scan<THREADS>(my_cnt, s_tot);
   if (tid < RADIX) {
@@ -391,7 +395,7 @@ __global__ void __launch_bounds__(THREADS, MINB)
   K* s_k = reinterpret_cast<K*>(smem + S::STAGE);
 #pragma unroll
   for (int j = 0; j < ITEMS; ++j) {
-    pos[j] += s_wh[warp * RADIX + digit_of(key[j], shift, mask)];
+    pos[j] += s_wh[warp * RADIX + digit_of(key[j], t.shift, t.mask)];
     s_k[pos[j]] = key[j];
   }
 
@@ -407,9 +411,9 @@ __global__ void __launch_bounds__(THREADS, MINB)
           gave_up = true;
           break;
         }
-        const uint32_t* p = &status[size_t(pred) * RADIX + tid];
+        const uint32_t* p = &t.status[size_t(pred) * RADIX + tid];
         uint32_t s = ld_relaxed(p);
-        if ((s & kFlagMask) == 0u) s = wait_status(p, ctrl, knobs.timeout_ns, tile);
+        if ((s & kFlagMask) == 0u) s = wait_status(p, ctrl, timeout_ns, tile);
         const uint32_t f = s & kFlagMask;
         if (f == kFlagErr) {
           gave_up = true;
@@ -419,15 +423,15 @@ __global__ void __launch_bounds__(THREADS, MINB)
         if (f == kFlagInc) break;
         --pred;
       }
-      if (!silent)
-        st_relaxed(&status[size_t(tile) * RADIX + tid],
+      if (!t.silent)
+        st_relaxed(&t.status[size_t(tile) * RADIX + tid],
                    gave_up ? kFlagErr : (kFlagInc | ((excl + my_cnt) & kValueMask)));
     }
     if (gave_up) s_misc[1] = 1u;
-    s_gbase[tid] = pass_offsets[tid] + excl - my_start;
+    s_gbase[tid] = t.pass_offsets[tid] + excl - my_start;
   }
   __syncthreads();
-  if (s_misc[1]) return;  // the output of this call is void; the host reads ctrl->error
+  if (s_misc[1]) return false;  // the output of this call is void; ctrl->error says why
 
   // scatter: consecutive threads take consecutive stage slots, which map to
   // consecutive output addresses inside each digit run
@@ -438,9 +442,9 @@ __global__ void __launch_bounds__(THREADS, MINB)
     gidx[s] = 0xffffffffu;
     if (i < tile_len) {
       const K k = s_k[i];
-      const uint32_t g = s_gbase[digit_of(k, shift, mask)] + i;
+      const uint32_t g = s_gbase[digit_of(k, t.shift, t.mask)] + i;
       if (g < n) {
-        kdst[g] = k;
+        t.kdst[g] = k;
         gidx[s] = g;
       } else {
         report_error(ctrl, kDevIndex, tile);
@@ -456,9 +460,47 @@ __global__ void __launch_bounds__(THREADS, MINB)
 #pragma unroll
     for (int s = 0; s < ITEMS; ++s) {
       const uint32_t i = uint32_t(s * THREADS + tid);
-      if (gidx[s] != 0xffffffffu) vdst[gidx[s]] = s_v[i];
+      if (gidx[s] != 0xffffffffu) t.vdst[gidx[s]] = s_v[i];
     }
   }
+  return true;
+}
+
+// One digit pass, one tile per CTA.  The grid has one CTA per tile; tile ids
+// come from an atomic counter so that a tile's predecessors have always
+// started before it (forward progress of the look-back).
+template <class K, int VB, int RADIX_BITS, int THREADS, int ITEMS, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB)
+    k_onesweep(K* __restrict__ k0, K* __restrict__ k1, ValT<VB>* __restrict__ v0,
+               ValT<VB>* __restrict__ v1, uint32_t n, int pass, uint32_t shift, uint32_t mask,
+               const uint32_t* __restrict__ pass_offsets, uint32_t* __restrict__ status,
+               Ctrl* __restrict__ ctrl, Knobs knobs) {
+  using S = OnesweepSmem<K, VB, RADIX_BITS, THREADS, ITEMS>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint32_t* s_misc = reinterpret_cast<uint32_t*>(smem + S::MISC);
+
+  const uint32_t exec = ctrl->exec_mask;
+  if (!((exec >> pass) & 1u)) return;  // every key has the same digit: nothing moves
+  const bool from_alt = (__popc(exec & ((1u << pass) - 1u)) & 1) != 0;
+  if (threadIdx.x == 0) {
+    s_misc[0] = atomicAdd(&ctrl->tile_counter[pass], 1u);
+    s_misc[2] = ld_relaxed(&ctrl->error);  // an earlier pass of this call gave up
+  }
+  __syncthreads();
+  if (s_misc[2] != 0u) return;  // CTA-uniform
+  TileArgs<K, VB> t;
+  t.ksrc = from_alt ? k1 : k0;
+  t.kdst = from_alt ? k0 : k1;
+  t.vsrc = from_alt ? v1 : v0;
+  t.vdst = from_alt ? v0 : v1;
+  t.n = n;
+  t.tile = s_misc[0];
+  t.shift = shift;
+  t.mask = mask;
+  t.pass_offsets = pass_offsets;
+  t.status = status;
+  t.silent = (int(t.tile) == knobs.drop_tile) && (pass == knobs.drop_pass);
+  onesweep_tile<K, VB, RADIX_BITS, THREADS, ITEMS, false>(t, ctrl, knobs.timeout_ns, smem);
 }
 
 // ------------------------------------------------------------ small sort
@@ -562,10 +604,16 @@ __device__ __forceinline__ void cta_sort(const K* kin, const ValT<VB>* vin, K* k
   }
 }
 
+// ctrl (may be null): the caller's workspace, whose status words this call
+// resets so that a later status read reports this call.
 template <class K, int VB, int RADIX_BITS, int THREADS, int ITEMS>
 __global__ void __launch_bounds__(THREADS, 1)
-    k_small_sort(K* keys, ValT<VB>* vals, uint32_t n, int begin_bit, int end_bit) {
+    k_small_sort(K* keys, ValT<VB>* vals, uint32_t n, int begin_bit, int end_bit, Ctrl* ctrl) {
   extern __shared__ __align__(16) unsigned char smem[];
+  if (ctrl != nullptr && threadIdx.x == 0) {
+    ctrl->error = 0u;
+    ctrl->error_info = 0u;
+  }
   cta_sort<K, VB, RADIX_BITS, THREADS, ITEMS>(keys, vals, keys, vals, n, begin_bit, end_bit,
                                               smem);
 }

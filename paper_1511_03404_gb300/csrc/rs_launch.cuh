@@ -118,8 +118,10 @@ struct SmallSort {
     if (prepare_kernel(reinterpret_cast<const void*>(kern), THREADS, S::BYTES) <= 0)
       return cudaErrorInvalidConfiguration;
     prof_before(a.stream);
+    Ctrl* ctrl = (a.ws != nullptr && a.ws_bytes >= sizeof(Ctrl)) ? static_cast<Ctrl*>(a.ws)
+                                                                  : nullptr;
     kern<<<1, THREADS, S::BYTES, a.stream>>>(static_cast<K*>(a.keys), static_cast<V*>(a.vals),
-                                             a.n, a.begin_bit, a.end_bit);
+                                             a.n, a.begin_bit, a.end_bit, ctrl);
     const cudaError_t e = cudaGetLastError();
     prof_after(a.stream, 2, 2.0 * double(a.n) * double(sizeof(K) + VB));
     return e;

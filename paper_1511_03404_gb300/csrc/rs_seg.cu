@@ -1,0 +1,119 @@
+// Host side of the batched segmented sort (32-bit key-value pairs):
+// workspace sizing and the launch sequence memset -> k_seg_plan ->
+// k_seg_persistent, all on the caller's stream (capturable in a CUDA graph).
+#include <algorithm>
+
+#include "../../include/rs.h"
+#include "rs_host.h"
+#include "rs_segmented.cuh"
+
+namespace rs {
+
+namespace {
+
+template <class K, int VB, int R, int THREADS, int ITEMS, int CHUNK_TILES>
+struct SegSort {
+  using C = SegKernelCfg<K, VB, R, THREADS, ITEMS, CHUNK_TILES>;
+  static constexpr int PLAN_THREADS = 1024;
+
+  static SegLayout layout(size_t n, size_t nseg, int passes) {
+    return seg_layout(n, nseg, passes, R, C::TILE, C::CHUNK);
+  }
+
+  static cudaError_t run(void* keys, void* vals, void* keys_alt, void* vals_alt, size_t n,
+                         const uint64_t* d_off, size_t nseg, int begin_bit, int end_bit,
+                         void* ws, cudaStream_t s, Knobs knobs) {
+    const int passes = num_passes(begin_bit, end_bit, R);
+    const SegLayout L = layout(n, nseg, passes);
+    char* w = static_cast<char*>(ws);
+    Ctrl* ctrl = reinterpret_cast<Ctrl*>(w);
+    cudaError_t e = cudaMemsetAsync(w, 0, L.memset_bytes, s);
+    if (e != cudaSuccess) return e;
+    k_seg_plan<PLAN_THREADS><<<1, PLAN_THREADS, 0, s>>>(
+        d_off, nseg, n, uint32_t(C::TILE), uint32_t(C::TILE), uint32_t(C::CHUNK), ctrl,
+        reinterpret_cast<uint32_t*>(w + L.small_ids), reinterpret_cast<SegDesc*>(w + L.descs),
+        reinterpret_cast<uint32_t*>(w + L.tile_seg), reinterpret_cast<uint32_t*>(w + L.chunk_seg),
+        L.tiles_max, L.chunks_max);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    auto kern = &k_seg_persistent<K, VB, R, THREADS, ITEMS, CHUNK_TILES>;
+    const int occ = prepare_kernel(reinterpret_cast<const void*>(kern), THREADS, C::BYTES);
+    if (occ <= 0) return cudaErrorInvalidConfiguration;
+    SegArgs a;
+    a.off = d_off;
+    a.begin_bit = begin_bit;
+    a.end_bit = end_bit;
+    a.passes = passes;
+    a.ctrl = ctrl;
+    a.small_ids = reinterpret_cast<const uint32_t*>(w + L.small_ids);
+    a.descs = reinterpret_cast<const SegDesc*>(w + L.descs);
+    a.tile_seg = reinterpret_cast<const uint32_t*>(w + L.tile_seg);
+    a.chunk_seg = reinterpret_cast<const uint32_t*>(w + L.chunk_seg);
+    a.state = reinterpret_cast<uint32_t*>(w + L.state);
+    a.counts = reinterpret_cast<uint32_t*>(w + L.counts);
+    a.offsets = reinterpret_cast<uint32_t*>(w + L.offsets);
+    a.status = reinterpret_cast<uint32_t*>(w + L.status);
+    a.tiles_max = L.tiles_max;
+    a.knobs = knobs;
+    using V = ValT<VB>;
+    const unsigned grid = unsigned(device_info().sms * occ);
+    prof_before(s);
+    kern<<<grid, THREADS, C::BYTES, s>>>(static_cast<K*>(keys), static_cast<V*>(vals),
+                                         static_cast<K*>(keys_alt), static_cast<V*>(vals_alt), a);
+    e = cudaGetLastError();
+    prof_after(s, RS_KERNEL_SEGMENTED,
+               double(n) * (sizeof(K) + passes * 2.0 * (sizeof(K) + VB)));
+    return e;
+  }
+};
+
+using SegU32Pairs = SegSort<uint32_t, 4, 8, 256, 16, 8>;
+
+}  // namespace
+
+Knobs knobs_now();
+
+}  // namespace rs
+
+using namespace rs;
+
+extern "C" {
+
+rs_status rs_segmented_workspace_bytes(size_t n, size_t n_seg, int begin_bit, int end_bit,
+                                       size_t* bytes) {
+  if (!bytes || begin_bit < 0 || begin_bit > end_bit || end_bit > 32) return RS_ERR_INVALID;
+  if (n >= (size_t(1) << 40) || n_seg >= (size_t(1) << 31)) return RS_ERR_INVALID;
+  *bytes = 0;
+  if (n == 0 || n_seg == 0 || begin_bit == end_bit) return RS_OK;
+  const SegLayout L = SegU32Pairs::layout(n, n_seg, num_passes(begin_bit, end_bit, 8));
+  if (L.tiles_max >= (size_t(1) << 32)) return RS_ERR_INVALID;
+  *bytes = L.total;
+  return RS_OK;
+}
+
+rs_status rs_segmented_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
+                                  uint32_t* vals_alt, size_t n, const uint64_t* d_offsets,
+                                  size_t n_seg, int begin_bit, int end_bit, void* ws,
+                                  size_t ws_bytes, rs_stream_t stream, int* result_in_alt) {
+  if (!result_in_alt) return RS_ERR_INVALID;
+  *result_in_alt = 0;
+  size_t need = 0;
+  rs_status st = rs_segmented_workspace_bytes(n, n_seg, begin_bit, end_bit, &need);
+  if (st != RS_OK) return st;
+  if (n == 0 || n_seg == 0 || begin_bit == end_bit) return RS_OK;
+  if (!keys || !vals || !keys_alt || !vals_alt || !d_offsets) return RS_ERR_INVALID;
+  if (keys == keys_alt || vals == vals_alt) return RS_ERR_INVALID;
+  auto al = [](const void* p, size_t a) { return reinterpret_cast<uintptr_t>(p) % a == 0; };
+  if (!al(keys, 4) || !al(vals, 4) || !al(keys_alt, 4) || !al(vals_alt, 4) || !al(d_offsets, 8))
+    return RS_ERR_INVALID;
+  if (!ws || ws_bytes < need || !al(ws, 256)) return RS_ERR_WORKSPACE;
+  const int passes = num_passes(begin_bit, end_bit, 8);
+  const cudaError_t e = SegU32Pairs::run(keys, vals, keys_alt, vals_alt, n, d_offsets, n_seg,
+                                         begin_bit, end_bit, ws,
+                                         reinterpret_cast<cudaStream_t>(stream), knobs_now());
+  if (e != cudaSuccess) return RS_ERR_CUDA;
+  *result_in_alt = passes & 1;
+  return RS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,378 @@
+// Batched segmented sort: the counting-sort passes of Sec. 2.6 applied
+// independently to every segment [off[s], off[s+1]) of one array, for all
+// segments in one persistent launch.
+//
+//   k_seg_plan        one CTA: classifies segments (short ones fit one CTA,
+//                     long ones are tiled), numbers the work items and maps
+//                     every histogram chunk and pass tile to its segment.
+//   k_seg_persistent  SMs x resident CTAs, each looping over one global work
+//                     queue (an atomic counter) in this order:
+//                       [histogram chunks of long segments]
+//                       [short segments: whole segment sorted in shared memory]
+//                       [pass 0 tiles of long segments] ... [pass P-1 tiles]
+//                     A tile of pass p waits (bounded) until its segment's
+//                     histograms are scanned and, for p > 0, until every tile
+//                     of pass p-1 of its segment is written.  Every wait is on
+//                     items taken from the queue earlier, which are held by
+//                     running CTAs, so the queue always makes progress.
+#pragma once
+
+#include "rs_kernels.cuh"
+
+namespace rs {
+
+constexpr uint32_t kDevInvalid = 1;  // RS_ERR_INVALID seen on the device
+
+struct SegDesc {
+  uint64_t off;    // first element
+  uint32_t len;    // elements
+  uint32_t tile0;  // first global pass tile
+  uint32_t chunk0; // first global histogram chunk
+  uint32_t seg;    // segment id
+  uint32_t pad[2];
+};
+static_assert(sizeof(SegDesc) == 32, "SegDesc is 32 bytes");
+
+// Per long segment: histogram ticket, ready flag, exec mask, done counters.
+constexpr int kSegStateWords = 16;
+enum SegStateField { kSegTicket = 0, kSegReady = 1, kSegExec = 2, kSegDone0 = 3 };
+
+// Plan results in Ctrl::tile_counter[]
+enum SegCtrlField {
+  kQueue = 0,    // work-queue ticket
+  kNSmall = 1,
+  kNLarge = 2,
+  kNTiles = 3,   // pass tiles of all long segments (one pass)
+  kNChunks = 4,  // histogram chunks of all long segments
+  kPlanned = 5   // 1 once the plan is complete
+};
+
+struct SegLayout {
+  size_t small_ids, descs, tile_seg, chunk_seg, state, counts, offsets, status, total;
+  size_t memset_bytes;  // Ctrl + state + counts
+  size_t tiles_max, chunks_max;
+};
+
+inline SegLayout seg_layout(size_t n, size_t nseg, int passes, int radix_bits, int tile,
+                            int chunk) {
+  SegLayout L{};
+  const size_t radix = size_t(1) << radix_bits;
+  L.tiles_max = (n + tile - 1) / tile + nseg;
+  L.chunks_max = (n + chunk - 1) / chunk + nseg;
+  L.state = 256;
+  L.counts = align_up(L.state + nseg * kSegStateWords * 4, 256);
+  L.memset_bytes = align_up(L.counts + nseg * passes * radix * 4, 256);
+  L.offsets = L.memset_bytes;
+  L.small_ids = align_up(L.offsets + nseg * passes * radix * 4, 256);
+  L.descs = align_up(L.small_ids + nseg * 4, 256);
+  L.tile_seg = align_up(L.descs + nseg * sizeof(SegDesc), 256);
+  L.chunk_seg = align_up(L.tile_seg + L.tiles_max * 4, 256);
+  L.status = align_up(L.chunk_seg + L.chunks_max * 4, 256);
+  L.total = align_up(L.status + size_t(passes) * L.tiles_max * radix * 4, 256);
+  return L;
+}
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Bounded wait until *p >= target.  False when it ran out or another CTA
+// already reported an error.
+__device__ __noinline__ static bool wait_geq(const uint32_t* p, uint32_t target, Ctrl* ctrl,
+                                             uint64_t timeout_ns, uint32_t info) {
+  if (ld_acquire(p) >= target) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 1;; ++it) {
+    if (ld_acquire(p) >= target) return true;
+    if ((it & 63u) == 0u) {
+      if (ld_relaxed(&ctrl->error) != 0u) return false;
+      if (global_ns() - t0 > timeout_ns) {
+        report_error(ctrl, kDevTimeout, info);
+        return false;
+      }
+    }
+  }
+}
+
+// One CTA numbers the work.  Segments longer than small_max are "long".
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS, 1)
+    k_seg_plan(const uint64_t* __restrict__ off, uint64_t nseg, uint64_t n, uint32_t small_max,
+               uint32_t tile, uint32_t chunk, Ctrl* __restrict__ ctrl,
+               uint32_t* __restrict__ small_ids, SegDesc* __restrict__ descs,
+               uint32_t* __restrict__ tile_seg, uint32_t* __restrict__ chunk_seg,
+               uint64_t tiles_max, uint64_t chunks_max) {
+  __shared__ uint32_t s_tot[32];
+  __shared__ uint32_t s_run[4];
+  __shared__ int s_bad;
+  const int tid = threadIdx.x;
+  if (tid < 4) s_run[tid] = 0u;
+  if (tid == 0) s_bad = 0;
+  __syncthreads();
+  if (off[0] != 0ull || off[nseg] != n) s_bad = 1;  // benign race: same value
+  for (uint64_t base = 0; base < nseg; base += THREADS) {
+    const uint64_t s = base + tid;
+    uint64_t len = 0;
+    bool valid = s < nseg;
+    if (valid) {
+      const uint64_t a = off[s], b = off[s + 1];
+      if (b < a || b > n || b - a > uint64_t((1u << 30) - 1u)) {
+        s_bad = 1;
+        valid = false;
+      } else {
+        len = b - a;
+      }
+    }
+    const bool is_long = valid && len > small_max;
+    const uint32_t small = (valid && !is_long) ? 1u : 0u;
+    const uint32_t lng = is_long ? 1u : 0u;
+    const uint32_t nt = is_long ? uint32_t((len + tile - 1) / tile) : 0u;
+    const uint32_t nc = is_long ? uint32_t((len + chunk - 1) / chunk) : 0u;
+    const uint32_t e_small = block_exclusive_scan<THREADS>(small, s_tot);
+    __syncthreads();
+    const uint32_t e_long = block_exclusive_scan<THREADS>(lng, s_tot);
+    __syncthreads();
+    const uint32_t e_tile = block_exclusive_scan<THREADS>(nt, s_tot);
+    __syncthreads();
+    const uint32_t e_chunk = block_exclusive_scan<THREADS>(nc, s_tot);
+    const uint32_t r_small = s_run[0], r_long = s_run[1], r_tile = s_run[2],
+                   r_chunk = s_run[3];
+    if (small) small_ids[r_small + e_small] = uint32_t(s);
+    if (is_long) {
+      const uint32_t li = r_long + e_long;
+      SegDesc d;
+      d.off = off[s];
+      d.len = uint32_t(len);
+      d.tile0 = r_tile + e_tile;
+      d.chunk0 = r_chunk + e_chunk;
+      d.seg = uint32_t(s);
+      d.pad[0] = d.pad[1] = 0u;
+      descs[li] = d;
+      if (uint64_t(d.tile0) + nt <= tiles_max && uint64_t(d.chunk0) + nc <= chunks_max) {
+        for (uint32_t i = 0; i < nt; ++i) tile_seg[d.tile0 + i] = li;
+        for (uint32_t i = 0; i < nc; ++i) chunk_seg[d.chunk0 + i] = li;
+      } else {
+        s_bad = 1;
+      }
+    }
+    __syncthreads();
+    if (tid == THREADS - 1) {  // the last thread's inclusive sums are the block totals
+      s_run[0] = r_small + e_small + small;
+      s_run[1] = r_long + e_long + lng;
+      s_run[2] = r_tile + e_tile + nt;
+      s_run[3] = r_chunk + e_chunk + nc;
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    if (s_bad) {
+      report_error(ctrl, kDevInvalid, 0u);
+      ctrl->tile_counter[kNSmall] = ctrl->tile_counter[kNLarge] = 0u;
+      ctrl->tile_counter[kNTiles] = ctrl->tile_counter[kNChunks] = 0u;
+    } else {
+      ctrl->tile_counter[kNSmall] = s_run[0];
+      ctrl->tile_counter[kNLarge] = s_run[1];
+      ctrl->tile_counter[kNTiles] = s_run[2];
+      ctrl->tile_counter[kNChunks] = s_run[3];
+    }
+    ctrl->tile_counter[kPlanned] = 1u;
+  }
+}
+
+template <class K, int VB, int RADIX_BITS, int THREADS, int ITEMS, int CHUNK_TILES>
+struct SegKernelCfg {
+  static constexpr int RADIX = 1 << RADIX_BITS;
+  static constexpr int TILE = THREADS * ITEMS;
+  static constexpr int CHUNK = TILE * CHUNK_TILES;
+  static constexpr int MAXP = (8 * int(sizeof(K)) + RADIX_BITS - 1) / RADIX_BITS;
+  static constexpr int HIST_BYTES = MAXP * (RADIX / 2) * 32 * 4;
+  using OS = OnesweepSmem<K, VB, RADIX_BITS, THREADS, ITEMS>;
+  using SS = SmallSmem<K, VB, RADIX_BITS, THREADS, ITEMS>;
+  static constexpr int A = OS::BYTES > SS::BYTES ? OS::BYTES : SS::BYTES;
+  static constexpr int BODY = A > HIST_BYTES ? A : HIST_BYTES;
+  static constexpr int MISC = (BODY + 15) / 16 * 16;  // u32 [8]
+  static constexpr int BYTES = MISC + 32;
+};
+
+struct SegArgs {
+  const uint64_t* off;
+  int begin_bit, end_bit, passes;
+  Ctrl* ctrl;
+  const uint32_t* small_ids;
+  const SegDesc* descs;
+  const uint32_t* tile_seg;
+  const uint32_t* chunk_seg;
+  uint32_t* state;    // [nseg][kSegStateWords]
+  uint32_t* counts;   // [nseg][passes][RADIX]
+  uint32_t* offsets;  // [nseg][passes][RADIX]
+  uint32_t* status;   // [passes][tiles_max][RADIX]
+  uint64_t tiles_max;
+  Knobs knobs;
+};
+
+template <class K, int VB, int RADIX_BITS, int THREADS, int ITEMS, int CHUNK_TILES>
+__global__ void __launch_bounds__(THREADS, 2)
+    k_seg_persistent(K* __restrict__ k0, ValT<VB>* __restrict__ v0, K* __restrict__ k1,
+                     ValT<VB>* __restrict__ v1, SegArgs a) {
+  using V = ValT<VB>;
+  using C = SegKernelCfg<K, VB, RADIX_BITS, THREADS, ITEMS, CHUNK_TILES>;
+  constexpr int RADIX = C::RADIX, HALF = RADIX / 2, TILE = C::TILE, CHUNK = C::CHUNK;
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint32_t* s_misc = reinterpret_cast<uint32_t*>(smem + C::MISC);
+  const int tid = threadIdx.x, lane = tid & 31;
+  Ctrl* ctrl = a.ctrl;
+  const int passes = a.passes;
+  // the sorted data of every segment ends where the pass count parity puts it
+  K* kout = (passes & 1) ? k1 : k0;
+  V* vout = (passes & 1) ? v1 : v0;
+
+  const uint32_t n_small = ctrl->tile_counter[kNSmall];
+  const uint32_t n_tiles = ctrl->tile_counter[kNTiles];
+  const uint32_t n_chunks = ctrl->tile_counter[kNChunks];
+  const uint32_t q_small = n_chunks;
+  const uint32_t q_pass = n_chunks + n_small;
+  const uint32_t q_end = q_pass + uint32_t(passes) * n_tiles;
+
+  for (;;) {
+    if (tid == 0) {
+      s_misc[0] = atomicAdd(&ctrl->tile_counter[kQueue], 1u);
+      s_misc[1] = ld_relaxed(&ctrl->error);
+    }
+    __syncthreads();
+    const uint32_t item = s_misc[0];
+    if (item >= q_end || s_misc[1] != 0u) break;  // CTA-uniform
+
+    if (item < q_small) {
+      // ---- digit histograms of one chunk of a long segment, every pass
+      const uint32_t li = a.chunk_seg[item];
+      const SegDesc d = a.descs[li];
+      const uint32_t lc = item - d.chunk0;
+      const uint32_t start = lc * uint32_t(CHUNK);
+      const uint32_t len = min(uint32_t(CHUNK), d.len - start);
+      const K* keys = k0 + d.off + start;
+      uint32_t* sh = reinterpret_cast<uint32_t*>(smem);
+      for (int i = tid; i < passes * HALF * 32; i += THREADS) sh[i] = 0u;
+      __syncthreads();
+      for (uint32_t i = tid; i < len; i += THREADS) {
+        const K k = keys[i];
+        for (int p = 0; p < passes; ++p) {
+          const int lo = a.begin_bit + p * RADIX_BITS;
+          const uint32_t m = (1u << (min(lo + RADIX_BITS, a.end_bit) - lo)) - 1u;
+          const uint32_t dg = digit_of(k, uint32_t(lo), m);
+          atomicAdd(&sh[(p * HALF + int(dg >> 1)) * 32 + lane], 1u << ((dg & 1u) << 4));
+        }
+      }
+      __syncthreads();
+      uint32_t* cnt = a.counts + size_t(li) * passes * RADIX;
+      for (int w = tid; w < passes * HALF; w += THREADS) {
+        uint32_t lo = 0u, hi = 0u;
+        const uint32_t* row = sh + w * 32;
+        for (int l = 0; l < 32; ++l) {
+          const uint32_t x = row[(l + lane) & 31];
+          lo += x & 0xFFFFu;
+          hi += x >> 16;
+        }
+        const int p = w / HALF, dg = (w - p * HALF) * 2;
+        if (lo) atomicAdd(&cnt[p * RADIX + dg], lo);
+        if (hi) atomicAdd(&cnt[p * RADIX + dg + 1], hi);
+      }
+      // clear the look-back words of this chunk's tiles, every pass
+      const uint32_t t_first = lc * uint32_t(CHUNK_TILES);
+      const uint32_t t_last = min(t_first + uint32_t(CHUNK_TILES), (d.len + TILE - 1) / TILE);
+      for (int p = 0; p < passes; ++p) {
+        uint32_t* st = a.status + (size_t(p) * a.tiles_max + d.tile0 + t_first) * RADIX;
+        const uint32_t words = (t_last - t_first) * RADIX;
+        for (uint32_t i = tid; i < words; i += THREADS) st[i] = 0u;
+      }
+      __threadfence();
+      __syncthreads();
+      uint32_t* state = a.state + size_t(li) * kSegStateWords;
+      if (tid == 0) {
+        const uint32_t chunks = (d.len + CHUNK - 1) / CHUNK;
+        s_misc[2] = atomicAdd(&state[kSegTicket], 1u) == chunks - 1u;
+      }
+      __syncthreads();
+      if (s_misc[2]) {
+        // last chunk of the segment: scan each pass's histogram
+        __threadfence();
+        uint32_t* offs = a.offsets + size_t(li) * passes * RADIX;
+        uint32_t exec = 0u;
+        for (int p = 0; p < passes; ++p) {
+          const uint32_t c = tid < RADIX ? ld_relaxed(&cnt[p * RADIX + tid]) : 0u;
+          const uint32_t e = block_exclusive_scan<THREADS>(c, reinterpret_cast<uint32_t*>(smem));
+          if (tid < RADIX) offs[p * RADIX + tid] = e;
+          if (!__syncthreads_or(tid < RADIX && c == d.len)) exec |= 1u << p;
+        }
+        if (tid == 0) {
+          if ((__popc(exec) & 1) != (passes & 1)) {
+            const uint32_t skipped = ~exec & ((1u << passes) - 1u);
+            exec |= skipped & (0u - skipped);
+          }
+          state[kSegExec] = exec;
+          __threadfence();
+          st_release(&state[kSegReady], 1u);
+        }
+      }
+    } else if (item < q_pass) {
+      // ---- one short segment, every pass in shared memory
+      const uint32_t s = a.small_ids[item - q_small];
+      const uint64_t b = a.off[s];
+      const uint32_t len = uint32_t(a.off[s + 1] - b);
+      cta_sort<K, VB, RADIX_BITS, THREADS, ITEMS>(k0 + b, v0 + b, kout + b, vout + b, len,
+                                                  a.begin_bit, a.end_bit, smem);
+    } else {
+      // ---- one tile of one pass of a long segment
+      const uint32_t q = item - q_pass;
+      const int p = int(q / n_tiles);
+      const uint32_t gt = q - uint32_t(p) * n_tiles;
+      const uint32_t li = a.tile_seg[gt];
+      const SegDesc d = a.descs[li];
+      uint32_t* state = a.state + size_t(li) * kSegStateWords;
+      const uint32_t ntiles = (d.len + TILE - 1) / TILE;
+      if (tid == 0) {
+        bool ok = wait_geq(&state[kSegReady], 1u, ctrl, a.knobs.timeout_ns, gt);
+        if (ok && p > 0) ok = wait_geq(&state[kSegDone0 + p - 1], ntiles, ctrl,
+                                       a.knobs.timeout_ns, gt);
+        s_misc[3] = ok ? 1u : 0u;
+        s_misc[4] = ld_relaxed(&state[kSegExec]);
+      }
+      __syncthreads();
+      const uint32_t exec = s_misc[4];
+      if (s_misc[3] && ((exec >> p) & 1u)) {
+        const bool from_alt = (__popc(exec & ((1u << p) - 1u)) & 1) != 0;
+        TileArgs<K, VB> t;
+        t.ksrc = (from_alt ? k1 : k0) + d.off;
+        t.kdst = (from_alt ? k0 : k1) + d.off;
+        if constexpr (VB > 0) {
+          t.vsrc = (from_alt ? v1 : v0) + d.off;
+          t.vdst = (from_alt ? v0 : v1) + d.off;
+        } else {
+          t.vsrc = nullptr;
+          t.vdst = nullptr;
+        }
+        t.n = d.len;
+        t.tile = gt - d.tile0;
+        const int lo = a.begin_bit + p * RADIX_BITS;
+        t.shift = uint32_t(lo);
+        t.mask = (1u << (min(lo + RADIX_BITS, a.end_bit) - lo)) - 1u;
+        t.pass_offsets = a.offsets + (size_t(li) * passes + p) * RADIX;
+        t.status = a.status + (size_t(p) * a.tiles_max + d.tile0) * RADIX;
+        t.silent = false;
+        onesweep_tile<K, VB, RADIX_BITS, THREADS, ITEMS, true>(t, ctrl, a.knobs.timeout_ns,
+                                                               smem);
+        __threadfence();
+      }
+      __syncthreads();
+      if (tid == 0) atomicAdd(&state[kSegDone0 + p], 1u);
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace rs

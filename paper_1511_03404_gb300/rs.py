@@ -63,6 +63,9 @@ _SIGS = {
     "rs_sort": ([_i, _i, _vp, _vp, _vp, _vp, _sz, _i, _i, _vp, _vp, _sz, _vp, _vp], _i),
     "rs_digit_counts": ([_i, _vp, _sz, _i, _i, _i, _vp, _vp, _vp, _vp, _sz, _vp], _i),
     "rs_workspace_status": ([_vp, _vp, _vp], _i),
+    "rs_segmented_sort_pairs": ([_vp, _vp, _vp, _vp, _sz, _vp, _sz, _i, _i, _vp, _sz, _vp, _vp],
+                                _i),
+    "rs_segmented_workspace_bytes": ([_sz, _sz, _i, _i, _vp], _i),
     "rs_profile_begin": ([_i], _i),
     "rs_profile_end": ([_vp, _vp, _vp], _i),
     "rs_debug_set": ([_i, ctypes.c_longlong], _i),
@@ -182,6 +185,21 @@ def rs_digit_counts(key_bytes, keys, n, begin_bit, end_bit, radix_bits, d_counts
                     d_exec_mask, ws, ws_bytes, stream):
     return load().rs_digit_counts(key_bytes, keys, n, begin_bit, end_bit, radix_bits, d_counts,
                                   d_offsets, d_exec_mask, ws, ws_bytes, stream)
+
+
+def rs_segmented_sort_pairs(keys, vals, keys_alt, vals_alt, n, d_offsets, n_seg, begin_bit,
+                            end_bit, ws, ws_bytes, stream):
+    r = _out_int()
+    st = load().rs_segmented_sort_pairs(keys, vals, keys_alt, vals_alt, n, d_offsets, n_seg,
+                                        begin_bit, end_bit, ws, ws_bytes, stream,
+                                        ctypes.byref(r))
+    return st, r.value
+
+
+def rs_segmented_workspace_bytes(n, n_seg, begin_bit=0, end_bit=32):
+    out = ctypes.c_size_t()
+    st = load().rs_segmented_workspace_bytes(n, n_seg, begin_bit, end_bit, ctypes.byref(out))
+    return st, out.value
 
 
 def rs_workspace_status(ws, stream):

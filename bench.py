@@ -82,7 +82,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -122,8 +122,8 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_inputs(n: int):
-    keys = {d: inputs.keys(np.uint32, d, n) for d in DISTS}
+def make_inputs(n: int, dists=DISTS):
+    keys = {d: inputs.keys(np.uint32, d, n) for d in dists}
     vals = inputs.values(np.uint32, n)
     return keys, vals
 
@@ -205,9 +205,10 @@ def run_ours(args):
     dev = torch.device("cuda", local if world > 1 else 0)
     torch.cuda.set_device(dev)
     n = args.n
-    keys_h, vals_h = make_inputs(n)
+    dists = (args.dist,) if args.dist else DISTS
+    keys_h, vals_h = make_inputs(n, dists)
     # pristine inputs on the device, plus the sort's double buffer and workspace
-    pristine = {d: torch.from_numpy(keys_h[d].view(np.int32)).to(dev) for d in DISTS}
+    pristine = {d: torch.from_numpy(keys_h[d].view(np.int32)).to(dev) for d in dists}
     vals0 = torch.from_numpy(vals_h.view(np.int32)).to(dev)
     k, v = torch.empty_like(vals0), torch.empty_like(vals0)
     ka, va = torch.empty_like(vals0), torch.empty_like(vals0)
@@ -219,7 +220,7 @@ def run_ours(args):
     h = stream.cuda_stream
 
     def one_sort(i, ev0=None, ev1=None):
-        d = DISTS[i % len(DISTS)]
+        d = dists[i % len(dists)]
         k.copy_(pristine[d])
         v.copy_(vals0)
         flush.fill_(i & 0xFF)
@@ -235,7 +236,7 @@ def run_ours(args):
     # correctness of the timed configuration: every distribution once, checked
     # against the properties that fix a stable sort (sorted keys, values are a
     # permutation, keys_in[vals_out] == keys_out, equal keys keep index order)
-    for i in range(len(DISTS)):
+    for i in range(0 if args.quick else len(dists)):
         d, in_alt = one_sort(i)
         st, info = rs.rs_workspace_status(ws.data_ptr(), h)
         rs.check(st, "device status")
@@ -268,8 +269,10 @@ def run_ours(args):
     value = world * args.steps * n / (total_ms / 1e3) / 1e9
 
     # end to end through the C ABI: pinned host -> device, sort, device -> host
-    e2e = e2e_rate(torch, rs, keys_h, vals_h, n, dev, ws, args)
-    if pg:
+    e2e = {"value": None, "ms_per_step": None, "h2d": 0, "d2h": 0}
+    if not args.quick:
+        e2e = e2e_rate(torch, rs, keys_h, vals_h, n, dev, ws, args, dists)
+    if pg and not args.quick:
         t = torch.tensor([e2e["ms_per_step"]], device=dev)
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
         e2e["value"] = world * n / (float(t.item()) / 1e3) / 1e9
@@ -306,8 +309,8 @@ def run_ours(args):
         "per_kernel": {k_: {"launches": p["launches"], "ms": p["ms"],
                             "GB/s": (p["bytes"] / 1e9) / (p["ms"] / 1e3) if p["ms"] else None}
                        for k_, p in prof.items() if p["launches"]},
-        "per_dist_ms": {d: statistics.mean(step_ms[i::len(DISTS)])
-                        for i, d in enumerate(DISTS) if step_ms[i::len(DISTS)]},
+        "per_dist_ms": {d: statistics.mean(step_ms[i::len(dists)])
+                        for i, d in enumerate(dists) if step_ms[i::len(dists)]},
         "cpu_baseline": None,
         "e2e": {"value": e2e["value"], "unit": "Gkeys/s",
                 "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]},
@@ -315,7 +318,7 @@ def run_ours(args):
         "clocks": clocks.summary(),
         "kernel_source": src,
     }
-    if not args.no_cpu_baseline:
+    if not (args.no_cpu_baseline or args.quick):
         line["cpu_baseline"] = cpu_oracle_rate(1 << 24)
         line["cpu_baseline"]["host"] = host_description()
     print(json.dumps(line), flush=True)
@@ -350,9 +353,9 @@ def check_sorted(torch, k_out, v_out, k_in) -> bool:
     return bool((idx[1:][eq] > idx[:-1][eq]).all())
 
 
-def e2e_rate(torch, rs, keys_h, vals_h, n, dev, ws, args) -> dict:
+def e2e_rate(torch, rs, keys_h, vals_h, n, dev, ws, args, dists) -> dict:
     """Host -> device copy, sort, device -> host copy, per step, through the C ABI."""
-    hk = {d: torch.from_numpy(keys_h[d].view(np.int32)).pin_memory() for d in DISTS}
+    hk = {d: torch.from_numpy(keys_h[d].view(np.int32)).pin_memory() for d in dists}
     hv = torch.from_numpy(vals_h.view(np.int32)).pin_memory()
     ok = torch.empty(n, dtype=torch.int32).pin_memory()
     ov = torch.empty(n, dtype=torch.int32).pin_memory()
@@ -362,7 +365,7 @@ def e2e_rate(torch, rs, keys_h, vals_h, n, dev, ws, args) -> dict:
     h = stream.cuda_stream
 
     def step(i):
-        d = DISTS[i % len(DISTS)]
+        d = dists[i % len(dists)]
         k.copy_(hk[d], non_blocking=True)
         v.copy_(hv, non_blocking=True)
         st, in_alt = rs.rs_sort_pairs_u32(k.data_ptr(), v.data_ptr(), ka.data_ptr(),
@@ -389,11 +392,16 @@ def e2e_rate(torch, rs, keys_h, vals_h, n, dev, ws, args) -> dict:
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=6)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--n", type=int, default=N_KEYS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true",
+                    help="timed sorts only (no CPU baseline, no end-to-end leg, no check); "
+                         "for profiler captures")
+    ap.add_argument("--dist", choices=DISTS, default=None,
+                    help="sort only this distribution (default: all six in turn)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

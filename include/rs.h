@@ -137,6 +137,33 @@ rs_status rs_sort_pairs_u64(uint64_t* keys, uint64_t* vals, uint64_t* keys_alt,
                             uint64_t* vals_alt, size_t n, int begin_bit, int end_bit, void* ws,
                             size_t ws_bytes, rs_stream_t stream, int* result_in_alt);
 
+/* Largest n that rs_sort_keys_u32_noalloc accepts. */
+#define RS_NOALLOC_MAX_N ((size_t)1 << 23)
+
+/*
+ * rs_sort_keys_u32 without a workspace argument and without allocating.
+ * The paper has no counterpart: this entry exists for callers that may not
+ * call cudaMalloc (or any allocator) at the point where they sort -- code
+ * running inside a framework that owns every device byte through its own
+ * pool, real-time or callback contexts where an allocation could block or
+ * synchronize the device, and systems whose memory must all be reserved at
+ * start-up.  The scratch it needs (about 8 MiB) is a fixed array of device
+ * memory inside this library, present on every GPU that loads the library
+ * until the process exits.
+ *   keys, keys_alt, n, begin_bit, end_bit, stream, result_in_alt: as for
+ *   rs_sort_keys_u32; n must not exceed RS_NOALLOC_MAX_N (else RS_ERR_INVALID,
+ *   nothing enqueued).
+ * The first call on each device looks up the array's device address (with
+ * that device current); make that first call before any stream capture.
+ * All calls on a device share the one array and each call leaves its
+ * contents behind (the next call clears what must start at zero): calls whose
+ * work may overlap on the GPU, for example on two streams, race and must be
+ * serialized by the caller.  Device-side status words are not reported back
+ * by this entry point.
+ */
+rs_status rs_sort_keys_u32_noalloc(uint32_t* keys, uint32_t* keys_alt, size_t n, int begin_bit,
+                                   int end_bit, rs_stream_t stream, int* result_in_alt);
+
 /*
  * Generic form of the four sorts above with an explicit configuration.
  * key_bytes is 4 or 8; val_bytes is 0 (keys only) or equal to key_bytes.

@@ -60,6 +60,7 @@ _SIGS = {
     "rs_sort_keys_u64": ([_vp, _vp, _sz, _i, _i, _vp, _sz, _vp, _vp], _i),
     "rs_sort_pairs_u32": ([_vp, _vp, _vp, _vp, _sz, _i, _i, _vp, _sz, _vp, _vp], _i),
     "rs_sort_pairs_u64": ([_vp, _vp, _vp, _vp, _sz, _i, _i, _vp, _sz, _vp, _vp], _i),
+    "rs_sort_keys_u32_noalloc": ([_vp, _vp, _sz, _i, _i, _vp, _vp], _i),
     "rs_sort": ([_i, _i, _vp, _vp, _vp, _vp, _sz, _i, _i, _vp, _vp, _sz, _vp, _vp], _i),
     "rs_digit_counts": ([_i, _vp, _sz, _i, _i, _i, _vp, _vp, _vp, _vp, _sz, _vp], _i),
     "rs_workspace_status": ([_vp, _vp, _vp], _i),
@@ -169,6 +170,16 @@ def rs_sort_pairs_u64(keys, vals, keys_alt, vals_alt, n, begin_bit, end_bit, ws,
     r = _out_int()
     st = load().rs_sort_pairs_u64(keys, vals, keys_alt, vals_alt, n, begin_bit, end_bit, ws,
                                   ws_bytes, stream, ctypes.byref(r))
+    return st, r.value
+
+
+RS_NOALLOC_MAX_N = 1 << 23
+
+
+def rs_sort_keys_u32_noalloc(keys, keys_alt, n, begin_bit, end_bit, stream):
+    r = _out_int()
+    st = load().rs_sort_keys_u32_noalloc(keys, keys_alt, n, begin_bit, end_bit, stream,
+                                         ctypes.byref(r))
     return st, r.value
 
 

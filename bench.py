@@ -318,6 +318,9 @@ def run_ours(args):
         "clocks": clocks.summary(),
         "kernel_source": src,
     }
+    if not (args.no_extras or args.quick) and world == 1:
+        line["segmented"] = bench_segmented(torch, rs, dev, args.seg_scaled)
+        line["serving"] = bench_serving(torch, rs, seconds=args.serve_seconds)
     if not (args.no_cpu_baseline or args.quick):
         line["cpu_baseline"] = cpu_oracle_rate(1 << 24)
         line["cpu_baseline"]["host"] = host_description()
@@ -389,6 +392,185 @@ def e2e_rate(torch, rs, keys_h, vals_h, n, dev, ws, args, dists) -> dict:
     return {"value": n / (ms / 1e3) / 1e9, "ms_per_step": ms, "h2d": 2 * 4 * n, "d2h": 2 * 4 * n}
 
 
+def bench_segmented(torch, rs, dev, scaled: bool, reps: int = 3) -> dict:
+    """20,000 segments of u32 pairs with log-uniform lengths in [1, 2^20]:
+    one batched launch sequence (captured once in a CUDA graph, replayed) vs
+    one plain rs_sort_pairs_u32 call per segment, same data, same stream."""
+    lengths = inputs.segment_lengths(20000, seed=1, max_log2=20)
+    law = "log-uniform in [1, 2^20], 20,000 segments, as stated"
+    if scaled:
+        lengths = inputs.scale_lengths(lengths, 1 << 28)
+        law = "log-uniform in [1, 2^20], 20,000 segments, scaled to total 2^28"
+    off = inputs.offsets_from_lengths(lengths)
+    n = int(off[-1])
+    keys = inputs.keys(np.uint32, "uniform", n, seed=1)
+    vals = np.arange(n, dtype=np.uint32)
+    pk = torch.from_numpy(keys.view(np.int32)).to(dev)
+    pv = torch.from_numpy(vals.view(np.int32)).to(dev)
+    del keys, vals
+    k, v = torch.empty_like(pk), torch.empty_like(pv)
+    ka, va = torch.empty_like(pk), torch.empty_like(pv)
+    doff = torch.from_numpy(off.view(np.int64)).to(dev)
+    st, need = rs.rs_segmented_workspace_bytes(n, len(lengths))
+    rs.check(st, "rs_segmented_workspace_bytes")
+    ws = torch.empty(need, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(dev)
+    h = stream.cuda_stream
+
+    def seg_call():
+        return rs.rs_segmented_sort_pairs(k.data_ptr(), v.data_ptr(), ka.data_ptr(),
+                                          va.data_ptr(), n, doff.data_ptr(), len(lengths), 0, 32,
+                                          ws.data_ptr(), ws.numel(), h)
+
+    with torch.cuda.stream(stream):
+        k.copy_(pk)
+        v.copy_(pv)
+        rs.check(seg_call()[0], "rs_segmented_sort_pairs")  # warm-up outside the capture
+    stream.synchronize()
+    rs.check(rs.rs_workspace_status(ws.data_ptr(), h)[0], "segmented device status")
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        st, in_alt = seg_call()
+    rs.check(st, "captured rs_segmented_sort_pairs")
+    batched = []
+    for _ in range(reps):
+        with torch.cuda.stream(stream):
+            k.copy_(pk)
+            v.copy_(pv)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        graph.replay()
+        with torch.cuda.stream(stream):
+            e1.record(stream)
+        stream.synchronize()
+        batched.append(e0.elapsed_time(e1))
+    rs.check(rs.rs_workspace_status(ws.data_ptr(), h)[0], "segmented device status")
+    # spot check: 64 segments against numpy's sort of the same slice
+    out_k = (ka if in_alt else k)
+    rng = np.random.default_rng(0)
+    for s in rng.choice(len(lengths), 64, replace=False):
+        a, b = int(off[s]), int(off[s + 1])
+        got = out_k[a:b].cpu().numpy().view(np.uint32)
+        want = np.sort(pk[a:b].cpu().numpy().view(np.uint32))
+        if not np.array_equal(got, want):
+            raise SystemExit(f"bench: segment {s} not sorted correctly")
+    # plain: one sort per segment through the typed entry point
+    maxlen = int(lengths.max())
+    st, need_p = rs.rs_workspace_bytes(4, 4, maxlen, 0, 32)
+    wsp = torch.empty(max(need_p, 256), dtype=torch.uint8, device=dev)
+    with torch.cuda.stream(stream):
+        k.copy_(pk)
+        v.copy_(pv)
+    stream.synchronize()
+    bk, bv, bka, bva = k.data_ptr(), v.data_ptr(), ka.data_ptr(), va.data_ptr()
+    offs = off.tolist()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for s in range(len(lengths)):
+        a = offs[s] * 4
+        st, _ = rs.rs_sort_pairs_u32(bk + a, bv + a, bka + a, bva + a, offs[s + 1] - offs[s], 0,
+                                     32, wsp.data_ptr(), wsp.numel(), h)
+        if st:
+            rs.check(st, "rs_sort_pairs_u32 (plain per segment)")
+    e1.record(stream)
+    stream.synchronize()
+    plain_ms = e0.elapsed_time(e1)
+    b_ms = min(batched)
+    out = {"law": law, "segments": len(lengths), "elements": n,
+           "batched_ms": b_ms, "batched_gkeys_s": n / (b_ms / 1e3) / 1e9,
+           "plain_ms": plain_ms, "plain_gkeys_s": n / (plain_ms / 1e3) / 1e9,
+           "batched_over_plain": plain_ms / b_ms,
+           "batched": "one CUDA graph replay: memset + planning kernel + one persistent kernel",
+           "plain": "one rs_sort_pairs_u32 call per segment on the same stream"}
+    del pk, pv, k, v, ka, va, ws, wsp
+    torch.cuda.empty_cache()
+    return out
+
+
+def bench_serving(torch, rs, seconds: float = 10.0, rate: float = 5000.0,
+                  budget: int = 24 << 30, streams: int = 8) -> dict:
+    """Poisson arrivals at `rate` requests/s of log-uniform size [2^10, 2^24],
+    half u32 pairs, half u64 keys (uniform keys), through the sort server
+    with a 24 GiB admission budget; p50/p99 latency and aggregate Gkeys/s."""
+    count = int(seconds * rate)
+    raw = inputs.mt19937(1, 3 * count)
+    u = raw.astype(np.float64) / 2.0**32
+    gaps = -np.log1p(-u[0::3][:count]) / rate
+    sizes = np.floor(2.0 ** (10 + 14 * u[1::3][:count])).astype(np.int64)
+    is_pairs = (raw[2::3][:count] % 2) == 0
+    pool_n = 1 << 25
+    k32 = torch.from_numpy(inputs.keys(np.uint32, "uniform", pool_n, seed=2).view(np.int32)).pin_memory()
+    k64 = torch.from_numpy(inputs.keys(np.uint64, "uniform", pool_n, seed=3).view(np.int64)).pin_memory()
+    iota = torch.arange(1 << 24, dtype=torch.int32).pin_memory()
+    ring_bytes = 6 << 30
+    ring = torch.empty(ring_bytes, dtype=torch.uint8).pin_memory()
+    ring_base = ring.data_ptr()
+    st, srv = rs.rs_server_create(budget, streams)
+    rs.check(st, "rs_server_create")
+    pending = {}        # handle -> (ring start, ring end)
+    live = []           # ring regions in use, in allocation order
+    head = 0
+    reqs = []           # keep the ctypes structs alive
+    offsets = (raw[0::3][:count].astype(np.int64) % (pool_n - (1 << 24)))
+
+    def reserve(nbytes):
+        nonlocal head
+        while True:
+            start = head if head + nbytes <= ring_bytes else 0
+            end = start + nbytes
+            if not any(a < end and start < b for a, b in live):
+                head = end
+                live.append((start, end))
+                return start
+            poll_some(block=True)
+
+    def poll_some(block=False):
+        for hnd in list(pending):
+            st_, done = rs.rs_poll(srv, hnd)
+            if done:
+                if st_ != rs.RS_OK:
+                    raise SystemExit(f"bench: server request failed: {rs.status_string(st_)}")
+                live.remove(pending.pop(hnd))
+        if block and pending:
+            time.sleep(0.0002)
+
+    arrival = np.cumsum(gaps)
+    t0 = time.perf_counter()
+    for i in range(count):
+        while time.perf_counter() - t0 < arrival[i]:
+            poll_some()
+        n = int(sizes[i])
+        o = int(offsets[i])
+        if is_pairs[i]:
+            out = reserve(8 * n)
+            r = rs.rs_request(4, 4, n, 0, 32, k32.data_ptr() + 4 * o, iota.data_ptr(),
+                              ring_base + out, ring_base + out + 4 * n)
+        else:
+            out = reserve(8 * n)
+            r = rs.rs_request(8, 0, n, 0, 64, k64.data_ptr() + 8 * o, None, ring_base + out, None)
+        st, hnd = rs.rs_submit(srv, r)
+        rs.check(st, "rs_submit")
+        reqs.append(r)
+        pending[hnd] = live[-1]
+        if len(reqs) > 4096:
+            reqs = reqs[-4096:]
+    while pending:
+        poll_some(block=True)
+    st, stats = rs.rs_server_stats(srv)
+    rs.check(st, "rs_server_stats")
+    rs.rs_server_destroy(srv)
+    offered = float(sizes.sum()) / float(arrival[-1]) / 1e9
+    return {"requests": count, "rate_per_s": rate, "budget_gib": budget / 2**30,
+            "streams": streams, "p50_ms": stats["p50_ms"], "p99_ms": stats["p99_ms"],
+            "max_ms": stats["max_ms"], "gkeys_per_s": stats["gkeys_per_s"],
+            "offered_gkeys_per_s": offered, "batches": stats["batches"],
+            "batched_requests": stats["batched_requests"], "max_queued": stats["max_queued"],
+            "pool_peak_gib": stats["pool_peak_bytes"] / 2**30,
+            "latency": "submit -> completion callback, host pinned buffers in and out"}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -400,6 +582,11 @@ def main(argv=None):
     ap.add_argument("--quick", action="store_true",
                     help="timed sorts only (no CPU baseline, no end-to-end leg, no check); "
                          "for profiler captures")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the segmented (batched vs plain) and serving measurements")
+    ap.add_argument("--seg-scaled", action="store_true",
+                    help="segment lengths scaled to a 2^28 total instead of the stated law")
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--dist", choices=DISTS, default=None,
                     help="sort only this distribution (default: all six in turn)")
     args = ap.parse_args(argv)

@@ -224,6 +224,73 @@ rs_status rs_segmented_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys
 rs_status rs_segmented_workspace_bytes(size_t n, size_t n_seg, int begin_bit, int end_bit,
                                        size_t* bytes);
 
+/* ---- sort server: continuous batching of requests on one GPU ---------- */
+
+/*
+ * A server owns one resident device-memory pool of `budget_bytes` (allocated
+ * once by rs_server_create) and `streams` CUDA streams on the device that is
+ * current at creation.  A scheduler thread admits queued requests, oldest
+ * first, whenever the request's device footprint fits the free part of the
+ * pool and a stream is free; a request that does not fit yet does not block
+ * younger ones that do.  Admitted 32-bit pair requests of at most 2^14
+ * elements (same bit range) are packed into one batched segmented sort;
+ * every other request runs as its own sort.  Each admitted unit runs
+ * copy-in, sort, copy-out on its stream, so units overlap on the device.
+ * The sorted result of a request does not depend on what it was batched or
+ * overlapped with.
+ */
+typedef struct rs_server rs_server;
+typedef uint64_t rs_handle;
+
+typedef struct rs_request {
+  int key_bytes;          /* 4 or 8 */
+  int val_bytes;          /* 0 or key_bytes */
+  size_t n;               /* elements, <= RS_MAX_N */
+  int begin_bit, end_bit; /* key bits to sort by */
+  const void* h_keys;     /* [n] host input keys (pinned memory lets copies overlap) */
+  const void* h_vals;     /* [n] host input values, or NULL when val_bytes is 0 */
+  void* h_out_keys;       /* [n] host output: the sorted keys */
+  void* h_out_vals;       /* [n] host output: the values in key order, or NULL */
+} rs_request;
+/* The host buffers must stay valid and untouched until rs_poll reports the
+ * request done.  Input and output may be the same buffers. */
+
+typedef struct rs_server_stats_t {
+  uint64_t completed, failed, keys;   /* requests done (ok / with an error), keys sorted */
+  uint64_t batches, batched_requests; /* segmented launches and the requests they carried */
+  uint64_t queued, max_queued;        /* requests waiting now / at most */
+  size_t pool_peak_bytes, pool_used_bytes;
+  double p50_ms, p99_ms, max_ms;      /* submit -> done latency of completed requests */
+  double wall_s;                      /* first submit -> last completion */
+  double gkeys_per_s;                 /* keys / wall_s / 1e9 */
+} rs_server_stats_t;
+
+/* Create a server: budget_bytes >= 1 MiB of device memory, 1..64 streams.
+ * RS_ERR_NOMEM if the pool cannot be allocated. */
+rs_status rs_server_create(size_t budget_bytes, int streams, rs_server** out);
+
+/* Stop the scheduler after the requests already on the GPU finish; queued
+ * requests end as RS_ERR_CANCELLED.  Frees the pool and the streams. */
+rs_status rs_server_destroy(rs_server* server);
+
+/* Queue a request without blocking.  RS_ERR_INVALID for a malformed request
+ * or one whose footprint exceeds the whole budget; RS_ERR_BUSY when the server
+ * is stopping or the queue is full. */
+rs_status rs_submit(rs_server* server, const rs_request* req, rs_handle* out);
+
+/* Non-blocking completion check.  *done = 0: still queued or running (returns
+ * RS_OK).  *done = 1: finished; the return value is the request's status
+ * (RS_OK, RS_ERR_CANCELLED, RS_ERR_TIMEOUT, ...) and the handle is retired
+ * (a later poll returns RS_ERR_NOT_FOUND). */
+rs_status rs_poll(rs_server* server, rs_handle handle, int* done);
+
+/* Cancel a request that has not started (RS_ERR_BUSY once it is on the GPU). */
+rs_status rs_cancel(rs_server* server, rs_handle handle);
+
+/* Latency percentiles, throughput and pool use since creation or the last reset. */
+rs_status rs_server_stats(rs_server* server, rs_server_stats_t* out);
+rs_status rs_server_reset_stats(rs_server* server);
+
 /* ---- per-kernel timing (CUDA events recorded on the sort's stream) ---- */
 
 /* Kinds of kernels the library launches. */

@@ -5,7 +5,7 @@ namespace rs {
 
 const Variant* variants_k64(int* count) {
   static const Variant table[] = {
-      OnesweepSort<uint64_t, 0, 8, 256, 16, 2>::describe(),
+      OnesweepSort<uint64_t, 0, 8, 256, 12, 3>::describe(),
       SmallSort<uint64_t, 0, 8, 512, 16>::describe(),
   };
   *count = int(sizeof(table) / sizeof(table[0]));

@@ -116,32 +116,30 @@ static __device__ __noinline__ uint32_t wait_status(const uint32_t* p, Ctrl* ctr
 // Digit histograms of every pass in one read of the keys, then (last CTA)
 // the exclusive scan of each and the set of passes that move data.
 //
-// Shared counters are 16-bit halves of 32-bit words laid out
-// [pass][digit/2][lane]: lane l only touches bank l, so a warp's 32
-// increments never conflict on a bank whatever the digits are (the zero and
-// sorted distributions included).  The 16-bit counters are drained into the
-// global counts before they can overflow.
-template <class K, int RADIX_BITS, int THREADS, int MAXP>
-__global__ void __launch_bounds__(THREADS)
+// Shared counters are laid out [pass][digit][slot] with slot = lane mod
+// SLOTS: with 32 slots (32-bit keys) lane l only ever touches bank l, so a
+// warp's 32 increments never meet on a bank whatever the digits are (the zero
+// and sorted distributions included).  64-bit keys have twice the passes and
+// use 16 slots to stay within shared memory.  FULL: the bit range is the whole
+// key and r = 8, so every digit is one byte, taken with a byte permute.
+template <class K, int RADIX_BITS, int THREADS, int MAXP, bool FULL>
+__global__ void __launch_bounds__(THREADS, 1)
     k_upsweep(const K* __restrict__ keys, uint32_t n, int begin_bit, int end_bit, int passes,
               uint32_t* __restrict__ counts, uint32_t* __restrict__ offsets,
               Ctrl* __restrict__ ctrl, uint4* __restrict__ zero_base, uint64_t zero_vec4) {
   constexpr int RADIX = 1 << RADIX_BITS;
-  constexpr int HALF = RADIX / 2;
-  constexpr int WARPS = THREADS / 32;
+  constexpr int SLOTS = sizeof(K) == 4 ? 32 : 16;
   constexpr int VEC = 16 / int(sizeof(K));
   constexpr int UNROLL = 4;
-  // each (pass, digit pair, lane) half-word gains at most WARPS*VEC*UNROLL
-  // per round, plus 2 from the scalar head and tail
-  constexpr uint32_t FLUSH_ROUNDS = (65535u - 2u) / uint32_t(WARPS * VEC * UNROLL);
   static_assert(RADIX <= THREADS, "one thread per digit in the scan");
-  static_assert(FLUSH_ROUNDS >= 1, "block too large for 16-bit counters");
+  static_assert(!FULL || RADIX_BITS == 8, "byte digits");
 
-  extern __shared__ uint32_t sh[];  // [passes][HALF][32]
+  extern __shared__ uint32_t sh[];  // [passes][RADIX][SLOTS]
   __shared__ uint32_t s_tot[32];
   __shared__ int s_last;
 
   const int tid = threadIdx.x, lane = tid & 31;
+  const uint32_t slot = uint32_t(lane & (SLOTS - 1));
   uint32_t shiftp[MAXP], maskp[MAXP];
 #pragma unroll
   for (int p = 0; p < MAXP; ++p) {
@@ -150,38 +148,25 @@ __global__ void __launch_bounds__(THREADS)
     shiftp[p] = p < passes ? uint32_t(lo) : 0u;
     maskp[p] = p < passes ? ((1u << (hi - lo)) - 1u) : 0u;
   }
-  const int words = passes * HALF * 32;
+  const int words = passes * RADIX * SLOTS;
   for (int i = tid; i < words; i += THREADS) sh[i] = 0u;
   __syncthreads();
 
   auto count_key = [&](K k) {
 #pragma unroll
     for (int p = 0; p < MAXP; ++p) {
-      if (p < passes) {
-        const uint32_t d = digit_of(k, shiftp[p], maskp[p]);
-        atomicAdd(&sh[(p * HALF + int(d >> 1)) * 32 + lane], 1u << ((d & 1u) << 4));
+      if (FULL || p < passes) {
+        uint32_t d;
+        if constexpr (FULL) {
+          const uint32_t half = (sizeof(K) == 8 && p >= 4) ? uint32_t(uint64_t(k) >> 32)
+                                                           : uint32_t(k);
+          d = __byte_perm(half, 0u, 0x4440u | uint32_t(p & 3));
+        } else {
+          d = digit_of(k, shiftp[p], maskp[p]);
+        }
+        atomicAdd(&sh[(p * RADIX + int(d)) * SLOTS + int(slot)], 1u);
       }
     }
-  };
-
-  auto flush = [&]() {
-    __syncthreads();
-    for (int w = tid; w < passes * HALF; w += THREADS) {
-      uint32_t lo = 0u, hi = 0u;
-      uint32_t* row = sh + w * 32;
-#pragma unroll 8
-      for (int l = 0; l < 32; ++l) {
-        const int c = (l + lane) & 31;  // rotated: lanes read distinct banks
-        const uint32_t x = row[c];
-        row[c] = 0u;
-        lo += x & 0xFFFFu;
-        hi += x >> 16;
-      }
-      const int p = w / HALF, d = (w - p * HALF) * 2;
-      if (lo) atomicAdd(&counts[p * RADIX + d], lo);
-      if (hi) atomicAdd(&counts[p * RADIX + d + 1], hi);
-    }
-    __syncthreads();
   };
 
   // 16-byte aligned body, scalar head and tail
@@ -196,11 +181,7 @@ __global__ void __launch_bounds__(THREADS)
   }
   const uint4* vp = reinterpret_cast<const uint4*>(keys + head);
   const uint32_t stride = gridDim.x * THREADS;
-  const uint32_t per_round = stride * UNROLL;
-  const uint32_t rounds = (nvec + per_round - 1u) / per_round;
-  uint32_t since = 0;
-  for (uint32_t r = 0; r < rounds; ++r) {
-    const uint32_t base = r * per_round + blockIdx.x * THREADS + tid;
+  for (uint32_t base = blockIdx.x * THREADS + tid; base < nvec; base += stride * UNROLL) {
     uint4 buf[UNROLL];
 #pragma unroll
     for (int u = 0; u < UNROLL; ++u) {
@@ -216,12 +197,16 @@ __global__ void __launch_bounds__(THREADS)
         for (int e = 0; e < VEC; ++e) count_key(ks[e]);
       }
     }
-    if (++since == FLUSH_ROUNDS && r + 1 < rounds) {
-      flush();
-      since = 0;
-    }
   }
-  flush();
+  __syncthreads();
+  // drain: one (pass, digit) per thread, summed over its slots
+  for (int w = tid; w < passes * RADIX; w += THREADS) {
+    const uint32_t* row = sh + w * SLOTS;
+    uint32_t c = 0u;
+#pragma unroll 8
+    for (int l = 0; l < SLOTS; ++l) c += row[(l + lane) & (SLOTS - 1)];  // rotated: no bank conflicts
+    if (c) atomicAdd(&counts[w], c);
+  }
 
   // clear the look-back status words of every pass of this call
   for (uint64_t i = uint64_t(blockIdx.x) * THREADS + tid; i < zero_vec4; i += stride)
@@ -267,9 +252,12 @@ struct OnesweepSmem {
   static constexpr int TSTART = CNT + RADIX * 4;           // u32 [RADIX] tile digit starts
   static constexpr int GBASE = TSTART + RADIX * 4;         // u32 [RADIX] global base
   static constexpr int TOT = GBASE + RADIX * 4;            // u32 [32]
-  static constexpr int MISC = TOT + 32 * 4;                // u32 [4]: tile, abort
-  static constexpr int STAGE = (MISC + 16 + 15) / 16 * 16; // TILE elements
-  static constexpr int BYTES = STAGE + TILE * ELEM;
+  static constexpr int MISC = TOT + 32 * 4;                // u32 [4]: tile, abort, ...
+  static constexpr int MBAR = MISC + 16;                   // u64 mbarrier of the tile loads
+  static constexpr int KIN = (MBAR + 8 + 15) / 16 * 16;    // tile keys as loaded (+16 B skew)
+  static constexpr int VIN = KIN + TILE * int(sizeof(K)) + 16;  // tile values as loaded
+  static constexpr int OUT = VIN + (VB > 0 ? TILE * VB + 16 : 0);  // sorted stage
+  static constexpr int BYTES = OUT + TILE * ELEM;
 };
 
 // Operands of one tile of one digit pass over one array (or one segment).
@@ -287,16 +275,104 @@ struct TileArgs {
   bool silent;                  // test-only: publish nothing for this tile
 };
 
-template <bool CG, class T>
-__device__ __forceinline__ T load_elem(const T* p) {
-  if constexpr (CG) return __ldcg(p);  // L2 only: written by other CTAs of this kernel
-  else return *p;
+// ---- bulk (TMA engine) copies global -> shared, completed on an mbarrier
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// One tile of one counting-sort pass (Sec. 2.6): rank, publish, look back,
-// stable scatter.  Every thread of the CTA calls it; it starts by clearing
-// the warp counters.  Returns false (CTA-uniform) when a bounded wait gave
-// up, in which case nothing of this tile was written.
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Before the barrier's shared memory is used for anything else.
+__device__ __forceinline__ void mbar_inval(uint64_t* bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0u;
+}
+
+// dst and src 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes,
+                                          uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Bounded wait for phase `parity` of the tile-load barrier.  False when the
+// limit ran out (the error is recorded); in that case the caller waits once
+// more, again bounded, so that no copy is still landing when it leaves.
+__device__ __noinline__ static bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                      Ctrl* ctrl, uint64_t timeout_ns,
+                                                      uint32_t info) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (;;) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > timeout_ns) {
+      report_error(ctrl, kDevTimeout, info);
+      return false;
+    }
+  }
+}
+
+// Shared-memory staging of elements [0, len) of src: element i lands at byte
+// (skew + i * sizeof(T)) of `buf`, skew = src address mod 16, so that the
+// 16-byte aligned middle ("body") goes by one bulk copy while the few head
+// and tail elements are loaded by threads.
+template <class T>
+struct Stage {
+  uint32_t skew, head, body, head_n, tail0;
+  __device__ __forceinline__ Stage(const T* src, uint32_t len) {
+    skew = uint32_t(reinterpret_cast<uintptr_t>(src) & 15u);
+    const uint32_t bytes = len * uint32_t(sizeof(T));
+    head = (16u - skew) & 15u;
+    if (head > bytes) head = bytes;
+    body = (bytes - head) & ~15u;
+    head_n = head / uint32_t(sizeof(T));
+    tail0 = (head + body) / uint32_t(sizeof(T));
+  }
+  __device__ __forceinline__ T* at(unsigned char* buf) const {
+    return reinterpret_cast<T*>(buf + skew);
+  }
+  // thread 0 only
+  __device__ __forceinline__ void issue(unsigned char* buf, const T* src, uint64_t* bar) const {
+    if (body)
+      bulk_load(buf + skew + head, reinterpret_cast<const unsigned char*>(src) + head, body, bar);
+  }
+  // every thread; L2 loads, since other CTAs of the same kernel may have
+  // written the source
+  __device__ __forceinline__ void edges(unsigned char* buf, const T* src, uint32_t len) const {
+    T* s = at(buf);
+    const uint32_t tid = threadIdx.x;
+    if (tid < head_n) s[tid] = __ldcg(src + tid);
+    if (tid < len - tail0) s[tail0 + tid] = __ldcg(src + tail0 + tid);
+  }
+};
+
+// One tile of one counting-sort pass (Sec. 2.6): stage the tile in shared
+// memory, rank it, publish its digit counts, look back, stable scatter.
+// Every thread of the CTA calls it.  Returns false (CTA-uniform) when a
+// bounded wait gave up, in which case nothing of this tile was written.
 template <class K, int VB, int RADIX_BITS, int THREADS, int ITEMS, bool CG>
 __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ctrl,
                                               uint64_t timeout_ns, unsigned char* smem) {
@@ -304,71 +380,89 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
   using S = OnesweepSmem<K, VB, RADIX_BITS, THREADS, ITEMS>;
   constexpr int RADIX = S::RADIX, WARPS = S::WARPS, TILE = S::TILE;
   static_assert(RADIX <= THREADS, "one thread per digit");
+  static_assert(TILE <= 65536, "stage slots fit 16 bits");
   uint32_t* s_wh = reinterpret_cast<uint32_t*>(smem + S::WH);
   uint32_t* s_cnt = reinterpret_cast<uint32_t*>(smem + S::CNT);
   uint32_t* s_tstart = reinterpret_cast<uint32_t*>(smem + S::TSTART);
   uint32_t* s_gbase = reinterpret_cast<uint32_t*>(smem + S::GBASE);
   uint32_t* s_tot = reinterpret_cast<uint32_t*>(smem + S::TOT);
   uint32_t* s_misc = reinterpret_cast<uint32_t*>(smem + S::MISC);
+  uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem + S::MBAR);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-
-  for (int i = tid; i < WARPS * RADIX; i += THREADS) s_wh[i] = 0u;
-  if (tid == 0) s_misc[1] = 0u;
-  __syncthreads();
 
   const uint32_t tile = t.tile, n = t.n;
   const uint32_t tile_base = tile * uint32_t(TILE);
   const uint32_t tile_len = min(uint32_t(TILE), n - tile_base);
 
-  // load: warp w owns tile elements [w*ITEMS*32, (w+1)*ITEMS*32), item j of
-  // lane l is element w*ITEMS*32 + j*32 + l (coalesced per item)
-  K key[ITEMS];
-  V val[ITEMS];
-  const uint32_t wbase = tile_base + uint32_t(warp * ITEMS * 32 + lane);
-  if (tile_len == uint32_t(TILE)) {
-#pragma unroll
-    for (int j = 0; j < ITEMS; ++j) key[j] = load_elem<CG>(t.ksrc + wbase + j * 32);
-    if constexpr (VB > 0) {
-#pragma unroll
-      for (int j = 0; j < ITEMS; ++j) val[j] = load_elem<CG>(t.vsrc + wbase + j * 32);
-    }
-  } else {
-    // past the end: the largest digit, so these items rank after every key
-    // of the tile and are never written
-#pragma unroll
-    for (int j = 0; j < ITEMS; ++j) {
-      const uint32_t i = wbase + j * 32;
-      key[j] = i < n ? load_elem<CG>(t.ksrc + i) : ~K(0);
-    }
-    if constexpr (VB > 0) {
-#pragma unroll
-      for (int j = 0; j < ITEMS; ++j) {
-        const uint32_t i = wbase + j * 32;
-        val[j] = i < n ? load_elem<CG>(t.vsrc + i) : V(0);
-      }
-    }
-  }
-
-  // rank within the warp: peers with the same digit found by match.any; the
-  // warp's running count per digit lives in its private shared counters
-  uint32_t pos[ITEMS];
-  {
-    uint32_t* wh = s_wh + warp * RADIX;
-    const uint32_t lt = lanemask_lt();
-#pragma unroll
-    for (int j = 0; j < ITEMS; ++j) {
-      const uint32_t d = digit_of(key[j], t.shift, t.mask);
-      const uint32_t peers = __match_any_sync(kFull, d);
-      const int leader = 31 - __clz(peers);
-      uint32_t before = 0u;
-      if (lane == leader) before = atomicAdd(&wh[d], uint32_t(__popc(peers)));
-      before = __shfl_sync(kFull, before, leader);
-      pos[j] = before + uint32_t(__popc(peers & lt));
-    }
+  if (tid == 0) {
+    mbar_init(s_bar);
+    s_misc[1] = 0u;
   }
   __syncthreads();
 
-  // per digit: exclusive prefix over warps, tile count, publish the count
+  // ---- stage the tile (keys, values) in shared memory
+  const K* gk = t.ksrc + tile_base;
+  const Stage<K> sk(gk, tile_len);
+  K* s_kin = sk.at(smem + S::KIN);
+  V* s_vin = nullptr;
+  if (tid == 0) {
+    uint32_t tx = sk.body;
+    if constexpr (VB > 0) tx += Stage<V>(t.vsrc + tile_base, tile_len).body;
+    // shared memory this CTA used through ordinary loads and stores before
+    // (an earlier work item) is about to be written by the copy engine; and,
+    // when the source was written by other CTAs of this kernel, those stores
+    // must be ordered before the copy engine reads them
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if constexpr (CG) asm volatile("fence.proxy.async.global;" ::: "memory");
+    mbar_arrive_expect_tx(s_bar, tx);
+    sk.issue(smem + S::KIN, gk, s_bar);
+    if constexpr (VB > 0) {
+      const Stage<V> sv(t.vsrc + tile_base, tile_len);
+      sv.issue(smem + S::VIN, t.vsrc + tile_base, s_bar);
+    }
+  }
+  sk.edges(smem + S::KIN, gk, tile_len);
+  if constexpr (VB > 0) {
+    const Stage<V> sv(t.vsrc + tile_base, tile_len);
+    s_vin = sv.at(smem + S::VIN);
+    sv.edges(smem + S::VIN, t.vsrc + tile_base, tile_len);
+  }
+  // past the end: the largest digit, so these items rank after every key of
+  // the tile and are never written out
+  for (uint32_t i = tile_len + tid; i < uint32_t(TILE); i += THREADS) s_kin[i] = ~K(0);
+  for (int i = tid; i < WARPS * RADIX; i += THREADS) s_wh[i] = 0u;
+  bool landed = mbar_wait_bounded(s_bar, 0u, ctrl, timeout_ns, tile);
+  if (!landed) landed = mbar_wait_bounded(s_bar, 0u, ctrl, timeout_ns, tile);
+  const int any_late = __syncthreads_or(!landed);
+  if (tid == 0) mbar_inval(s_bar);  // its memory may serve other work items later
+  if (any_late) return false;       // CTA-uniform
+
+  // ---- rank within the warp: warp w owns tile slots [w*ITEMS*32, (w+1)*ITEMS*32),
+  // item j of lane l is slot w*ITEMS*32 + j*32 + l.  Peers with the same digit
+  // come from match.any; the warp's running count per digit is in its private
+  // shared counters.  The three loops are independent across items, so the
+  // latencies of the match, the atomic and the shuffle overlap.
+  const uint32_t slot0 = uint32_t(warp * ITEMS * 32 + lane);
+  uint32_t dg[ITEMS], peers[ITEMS], pos[ITEMS];
+#pragma unroll
+  for (int j = 0; j < ITEMS; ++j) dg[j] = digit_of(s_kin[slot0 + j * 32], t.shift, t.mask);
+#pragma unroll
+  for (int j = 0; j < ITEMS; ++j) peers[j] = __match_any_sync(kFull, dg[j]);
+  {
+    uint32_t* wh = s_wh + warp * RADIX;
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+      pos[j] = 0u;
+      if (lane == 31 - __clz(peers[j])) pos[j] = atomicAdd(&wh[dg[j]], uint32_t(__popc(peers[j])));
+    }
+    const uint32_t lt = lanemask_lt();
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j)
+      pos[j] = __shfl_sync(kFull, pos[j], 31 - __clz(peers[j])) + uint32_t(__popc(peers[j] & lt));
+  }
+  __syncthreads();
+
+  // ---- per digit: exclusive prefix over warps, tile count, publish the count
   uint32_t my_cnt = 0u;
   if (tid < RADIX) {
     uint32_t run = 0u;
@@ -391,15 +485,15 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
   for (int i = tid; i < WARPS * RADIX; i += THREADS) s_wh[i] += s_tstart[i & (RADIX - 1)];
   __syncthreads();
 
-  // local positions; keys into the stage in (digit, input) order
-  K* s_k = reinterpret_cast<K*>(smem + S::STAGE);
+  // ---- keys into the stage in (digit, input) order
+  K* s_out = reinterpret_cast<K*>(smem + S::OUT);
 #pragma unroll
   for (int j = 0; j < ITEMS; ++j) {
-    pos[j] += s_wh[warp * RADIX + digit_of(key[j], t.shift, t.mask)];
-    s_k[pos[j]] = key[j];
+    pos[j] += s_wh[warp * RADIX + dg[j]];
+    s_out[pos[j]] = s_kin[slot0 + j * 32];
   }
 
-  // decoupled look-back: sum the counts of the preceding tiles for my digit
+  // ---- decoupled look-back: sum the counts of the preceding tiles for my digit
   if (tid < RADIX) {
     uint32_t excl = 0u;
     bool gave_up = false;
@@ -412,14 +506,14 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
           break;
         }
         const uint32_t* p = &t.status[size_t(pred) * RADIX + tid];
-        uint32_t s = ld_relaxed(p);
-        if ((s & kFlagMask) == 0u) s = wait_status(p, ctrl, timeout_ns, tile);
-        const uint32_t f = s & kFlagMask;
+        uint32_t sw = ld_relaxed(p);
+        if ((sw & kFlagMask) == 0u) sw = wait_status(p, ctrl, timeout_ns, tile);
+        const uint32_t f = sw & kFlagMask;
         if (f == kFlagErr) {
           gave_up = true;
           break;
         }
-        excl += s & kValueMask;
+        excl += sw & kValueMask;
         if (f == kFlagInc) break;
         --pred;
       }
@@ -433,15 +527,15 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
   __syncthreads();
   if (s_misc[1]) return false;  // the output of this call is void; ctrl->error says why
 
-  // scatter: consecutive threads take consecutive stage slots, which map to
-  // consecutive output addresses inside each digit run
+  // ---- scatter: consecutive threads take consecutive stage slots, which map
+  // to consecutive output addresses inside each digit run
   uint32_t gidx[ITEMS];
 #pragma unroll
   for (int s = 0; s < ITEMS; ++s) {
     const uint32_t i = uint32_t(s * THREADS + tid);
     gidx[s] = 0xffffffffu;
     if (i < tile_len) {
-      const K k = s_k[i];
+      const K k = s_out[i];
       const uint32_t g = s_gbase[digit_of(k, t.shift, t.mask)] + i;
       if (g < n) {
         t.kdst[g] = k;
@@ -453,14 +547,14 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
   }
   if constexpr (VB > 0) {
     __syncthreads();
-    V* s_v = reinterpret_cast<V*>(smem + S::STAGE);
+    V* s_vout = reinterpret_cast<V*>(smem + S::OUT);
 #pragma unroll
-    for (int j = 0; j < ITEMS; ++j) s_v[pos[j]] = val[j];
+    for (int j = 0; j < ITEMS; ++j) s_vout[pos[j]] = s_vin[slot0 + j * 32];
     __syncthreads();
 #pragma unroll
     for (int s = 0; s < ITEMS; ++s) {
       const uint32_t i = uint32_t(s * THREADS + tid);
-      if (gidx[s] != 0xffffffffu) t.vdst[gidx[s]] = s_v[i];
+      if (gidx[s] != 0xffffffffu) t.vdst[gidx[s]] = s_vout[i];
     }
   }
   return true;

@@ -30,18 +30,21 @@ struct OnesweepSort {
     Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws);
     cudaError_t e = cudaMemsetAsync(ws, 0, L.memset_bytes, a.stream);
     if (e != cudaSuccess) return e;
-    const void* f = reinterpret_cast<const void*>(&k_upsweep<K, R, UP_THREADS, MAXP>);
-    const int max_smem = MAXP * (RADIX / 2) * 32 * 4;
-    const int occ = prepare_kernel(f, UP_THREADS, max_smem);
+    const bool full = R == 8 && a.begin_bit == 0 && a.end_bit == 8 * int(sizeof(K));
+    auto kern = full ? &k_upsweep<K, R, UP_THREADS, MAXP, (R == 8)>
+                     : &k_upsweep<K, R, UP_THREADS, MAXP, false>;
+    constexpr int SLOTS = sizeof(K) == 4 ? 32 : 16;
+    const int max_smem = MAXP * RADIX * SLOTS * 4;
+    const int occ = prepare_kernel(reinterpret_cast<const void*>(kern), UP_THREADS, max_smem);
     if (occ <= 0) return cudaErrorInvalidConfiguration;
-    const int smem = passes * (RADIX / 2) * 32 * 4;
+    const int smem = passes * RADIX * SLOTS * 4;
     constexpr uint32_t per_cta = UP_THREADS * (16 / sizeof(K)) * 4;
     const uint32_t want = (a.n + per_cta - 1) / per_cta;
     const uint32_t grid =
         std::max(1u, std::min(uint32_t(device_info().sms * occ), want));
     const uint64_t zero_vec4 = clear_status ? L.status_bytes / 16 : 0;
     prof_before(a.stream);
-    k_upsweep<K, R, UP_THREADS, MAXP><<<grid, UP_THREADS, smem, a.stream>>>(
+    kern<<<grid, UP_THREADS, smem, a.stream>>>(
         static_cast<const K*>(a.keys), a.n, a.begin_bit, a.end_bit, passes,
         reinterpret_cast<uint32_t*>(ws + L.counts), reinterpret_cast<uint32_t*>(ws + L.offsets),
         ctrl, reinterpret_cast<uint4*>(ws + L.status), zero_vec4);

@@ -1,0 +1,546 @@
+// Sort server: continuous batching of sort requests on one GPU.
+//
+// A scheduler thread admits queued requests while their device footprint
+// fits the memory budget (one resident device pool, carved by a first-fit
+// allocator) and while stream slots are free.  Admitted short 32-bit pair
+// requests are packed into one batched segmented sort; every other request
+// runs as its own sort.  Each admitted unit goes to one of several CUDA
+// streams, so copies and sorts of different requests overlap on the device,
+// and requests that arrive while others run are admitted as memory and slots
+// free up.  A host callback at the end of each unit's stream work marks its
+// requests done; rs_poll reports that without blocking.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/rs.h"
+#include "rs_common.h"
+#include "rs_host.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+double now_s() {
+  return std::chrono::duration<double>(Clock::now().time_since_epoch()).count();
+}
+
+// First-fit allocator over [0, size) with coalescing free blocks.
+class Pool {
+ public:
+  explicit Pool(size_t size) : size_(size) { free_[0] = size; }
+  bool alloc(size_t bytes, size_t* off) {
+    bytes = rs::align_up(std::max<size_t>(bytes, 256), 256);
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= bytes) {
+        *off = it->first;
+        const size_t rest = it->second - bytes;
+        const size_t noff = it->first + bytes;
+        free_.erase(it);
+        if (rest) free_[noff] = rest;
+        used_ += bytes;
+        peak_ = std::max(peak_, used_);
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(size_t off, size_t bytes) {
+    bytes = rs::align_up(std::max<size_t>(bytes, 256), 256);
+    used_ -= bytes;
+    auto it = free_.emplace(off, bytes).first;
+    auto next = std::next(it);
+    if (next != free_.end() && it->first + it->second == next->first) {
+      it->second += next->second;
+      free_.erase(next);
+    }
+    if (it != free_.begin()) {
+      auto prev = std::prev(it);
+      if (prev->first + prev->second == it->first) {
+        prev->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+  size_t used() const { return used_; }
+  size_t peak() const { return peak_; }
+
+ private:
+  size_t size_, used_ = 0, peak_ = 0;
+  std::map<size_t, size_t> free_;
+};
+
+struct Request {
+  uint64_t id = 0;
+  rs_request req{};
+  int state = 0;  // 0 queued, 1 running, 2 done
+  rs_status status = RS_OK;
+  double t_submit = 0, t_done = 0;
+};
+
+struct Unit;  // one admitted sort or batch
+
+}  // namespace
+
+struct rs_server {
+  int device = 0;
+  size_t budget = 0;
+  char* pool_base = nullptr;
+  std::unique_ptr<Pool> pool;
+  std::vector<cudaStream_t> streams;
+  std::vector<int> stream_busy;
+  size_t batch_max_n = 1u << 14;  // requests up to this size share a segmented launch
+  size_t max_batch_keys = 1u << 22;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<uint64_t> pending;
+  std::unordered_map<uint64_t, std::shared_ptr<Request>> reqs;
+  std::vector<Unit*> finished;  // completed units, handed over by the host callbacks
+  uint64_t changes = 0;         // bumped by every submit, cancel and completion
+  uint32_t* status_slab = nullptr;  // pinned, one device-status word per stream
+  uint64_t next_id = 1;
+  bool stop = false;
+  std::thread sched;
+  // statistics
+  std::vector<double> latencies;
+  uint64_t completed = 0, failed = 0, keys_done = 0, batches = 0, batched_requests = 0;
+  double first_submit = 0, last_done = 0;
+  size_t max_queue = 0;
+};
+
+namespace {
+
+struct Unit {
+  rs_server* srv = nullptr;
+  std::vector<std::shared_ptr<Request>> members;
+  size_t pool_off = 0, pool_bytes = 0;
+  int stream = 0;
+  uint32_t* h_status = nullptr;  // pinned: device status word of the sort
+};
+
+
+bool valid_request(const rs_request& r) {
+  if (!((r.key_bytes == 4 || r.key_bytes == 8) && (r.val_bytes == 0 || r.val_bytes == r.key_bytes)))
+    return false;
+  if (r.n > RS_MAX_N || r.begin_bit < 0 || r.begin_bit > r.end_bit || r.end_bit > 8 * r.key_bytes)
+    return false;
+  if (r.n && (!r.h_keys || !r.h_out_keys)) return false;
+  if (r.n && r.val_bytes && (!r.h_vals || !r.h_out_vals)) return false;
+  return true;
+}
+
+// Device layout of one request's unit: keys, values, their alternates, workspace.
+struct SingleLayout {
+  size_t k, v, ka, va, ws, ws_bytes, total;
+};
+
+SingleLayout single_layout(const rs_request& r) {
+  SingleLayout L;
+  size_t ws = 0;
+  rs_workspace_bytes(r.key_bytes, r.val_bytes, r.n, r.begin_bit, r.end_bit, nullptr, &ws);
+  const size_t kb = rs::align_up(r.n * size_t(r.key_bytes), 256);
+  const size_t vb = rs::align_up(r.n * size_t(r.val_bytes), 256);
+  L.k = 0;
+  L.v = L.k + kb;
+  L.ka = L.v + vb;
+  L.va = L.ka + kb;
+  L.ws = L.va + vb;
+  L.ws_bytes = rs::align_up(std::max<size_t>(ws, 256), 256);
+  L.total = L.ws + L.ws_bytes;
+  return L;
+}
+
+size_t single_footprint(const rs_request& r) { return single_layout(r).total; }
+
+bool batchable(const rs_server* s, const rs_request& r) {
+  return r.key_bytes == 4 && r.val_bytes == 4 && r.n <= s->batch_max_n && r.n > 1;
+}
+
+void CUDART_CB on_unit_done(void* p) {
+  Unit* u = static_cast<Unit*>(p);
+  rs_server* s = u->srv;
+  const double t = now_s();
+  {
+    std::lock_guard<std::mutex> g(s->mu);
+    for (auto& m : u->members) m->t_done = t;
+    s->finished.push_back(u);
+    s->changes += 1;
+  }
+  s->cv.notify_all();
+}
+
+// Enqueue copies in, the sort, copies out and the completion callback.
+rs_status launch_single(rs_server* s, Unit* u) {
+  Request& r = *u->members[0];
+  const rs_request& q = r.req;
+  cudaStream_t st = s->streams[u->stream];
+  char* base = s->pool_base + u->pool_off;
+  const size_t kbytes = q.n * q.key_bytes, vbytes = q.n * q.val_bytes;
+  const SingleLayout L = single_layout(q);
+  char* k = base + L.k;
+  char* v = base + L.v;
+  char* ka = base + L.ka;
+  char* va = base + L.va;
+  char* ws = base + L.ws;
+  const size_t ws_bytes = L.ws_bytes;
+  if (cudaMemcpyAsync(k, q.h_keys, kbytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return RS_ERR_CUDA;
+  if (vbytes && cudaMemcpyAsync(v, q.h_vals, vbytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return RS_ERR_CUDA;
+  int in_alt = 0;
+  rs_status rs_st = rs_sort(q.key_bytes, q.val_bytes, k, vbytes ? v : nullptr, ka,
+                            vbytes ? va : nullptr, q.n, q.begin_bit, q.end_bit, nullptr, ws,
+                            ws_bytes, reinterpret_cast<rs_stream_t>(st), &in_alt);
+  if (rs_st != RS_OK) return rs_st;
+  if (cudaMemcpyAsync(u->h_status, ws, sizeof(uint32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return RS_ERR_CUDA;
+  if (cudaMemcpyAsync(q.h_out_keys, in_alt ? ka : k, kbytes, cudaMemcpyDeviceToHost, st) !=
+      cudaSuccess)
+    return RS_ERR_CUDA;
+  if (vbytes && cudaMemcpyAsync(q.h_out_vals, in_alt ? va : v, vbytes, cudaMemcpyDeviceToHost,
+                                st) != cudaSuccess)
+    return RS_ERR_CUDA;
+  if (cudaLaunchHostFunc(st, on_unit_done, u) != cudaSuccess) return RS_ERR_CUDA;
+  return RS_OK;
+}
+
+struct BatchPlan {
+  size_t total = 0, seg_ws = 0;
+  size_t k, v, ka, va, off, ws, bytes;
+};
+
+BatchPlan plan_batch(size_t total, size_t nseg) {
+  BatchPlan b;
+  b.total = total;
+  rs_segmented_workspace_bytes(total, nseg, 0, 32, &b.seg_ws);
+  const size_t arr = rs::align_up(total * 4, 256);
+  b.k = 0;
+  b.v = b.k + arr;
+  b.ka = b.v + arr;
+  b.va = b.ka + arr;
+  b.off = b.va + arr;
+  b.ws = b.off + rs::align_up((nseg + 1) * 8, 256);
+  b.bytes = b.ws + rs::align_up(std::max<size_t>(b.seg_ws, 256), 256);
+  return b;
+}
+
+rs_status launch_batch(rs_server* s, Unit* u, const BatchPlan& b) {
+  cudaStream_t st = s->streams[u->stream];
+  char* base = s->pool_base + u->pool_off;
+  const size_t nseg = u->members.size();
+  std::vector<uint64_t> off(nseg + 1, 0);
+  for (size_t i = 0; i < nseg; ++i) off[i + 1] = off[i] + u->members[i]->req.n;
+  // every member in a batch has the same bit range (the scheduler groups them)
+  const int begin_bit = u->members[0]->req.begin_bit, end_bit = u->members[0]->req.end_bit;
+  for (size_t i = 0; i < nseg; ++i) {
+    const rs_request& q = u->members[i]->req;
+    if (cudaMemcpyAsync(base + b.k + off[i] * 4, q.h_keys, q.n * 4, cudaMemcpyHostToDevice, st) ||
+        cudaMemcpyAsync(base + b.v + off[i] * 4, q.h_vals, q.n * 4, cudaMemcpyHostToDevice, st))
+      return RS_ERR_CUDA;
+  }
+  // pageable source: the call returns once the offsets are staged
+  if (cudaMemcpyAsync(base + b.off, off.data(), (nseg + 1) * 8, cudaMemcpyHostToDevice, st))
+    return RS_ERR_CUDA;
+  int in_alt = 0;
+  rs_status rs_st = rs_segmented_sort_pairs(
+      reinterpret_cast<uint32_t*>(base + b.k), reinterpret_cast<uint32_t*>(base + b.v),
+      reinterpret_cast<uint32_t*>(base + b.ka), reinterpret_cast<uint32_t*>(base + b.va), b.total,
+      reinterpret_cast<const uint64_t*>(base + b.off), nseg, begin_bit, end_bit, base + b.ws,
+      b.bytes - b.ws, reinterpret_cast<rs_stream_t>(st), &in_alt);
+  if (rs_st != RS_OK) return rs_st;
+  if (cudaMemcpyAsync(u->h_status, base + b.ws, sizeof(uint32_t), cudaMemcpyDeviceToHost, st))
+    return RS_ERR_CUDA;
+  const size_t ko = in_alt ? b.ka : b.k, vo = in_alt ? b.va : b.v;
+  for (size_t i = 0; i < nseg; ++i) {
+    const rs_request& q = u->members[i]->req;
+    if (cudaMemcpyAsync(q.h_out_keys, base + ko + off[i] * 4, q.n * 4, cudaMemcpyDeviceToHost,
+                        st) ||
+        cudaMemcpyAsync(q.h_out_vals, base + vo + off[i] * 4, q.n * 4, cudaMemcpyDeviceToHost, st))
+      return RS_ERR_CUDA;
+  }
+  if (cudaLaunchHostFunc(st, on_unit_done, u) != cudaSuccess) return RS_ERR_CUDA;
+  return RS_OK;
+}
+
+int free_stream(rs_server* s) {
+  for (size_t i = 0; i < s->streams.size(); ++i)
+    if (!s->stream_busy[i]) return int(i);
+  return -1;
+}
+
+void finish_unit(rs_server* s, Unit* u, rs_status st) {
+  // caller holds s->mu
+  s->pool->release(u->pool_off, u->pool_bytes);
+  s->stream_busy[u->stream] = 0;
+  rs_status dev = RS_OK;
+  if (st == RS_OK && u->h_status && *u->h_status != 0u)
+    dev = (*u->h_status == rs::kDevTimeout) ? RS_ERR_TIMEOUT
+          : (*u->h_status == 1u)            ? RS_ERR_INVALID
+                                            : RS_ERR_DEVICE;
+  for (auto& m : u->members) {
+    m->state = 2;
+    m->status = st != RS_OK ? st : dev;
+    if (m->t_done == 0) m->t_done = now_s();
+    if (m->status == RS_OK) {
+      s->completed += 1;
+      s->keys_done += m->req.n;
+      s->latencies.push_back(m->t_done - m->t_submit);
+      s->last_done = std::max(s->last_done, m->t_done);
+    } else {
+      s->failed += 1;
+    }
+  }
+  delete u;
+}
+
+void scheduler(rs_server* s) {
+  cudaSetDevice(s->device);
+  std::unique_lock<std::mutex> lk(s->mu);
+  uint64_t seen = ~0ull;
+  while (true) {
+    // sleep until something changed: a submission, a cancel or a completion
+    s->cv.wait(lk, [&] { return s->stop || s->changes != seen; });
+    seen = s->changes;
+    for (Unit* u : s->finished) finish_unit(s, u, RS_OK);
+    s->finished.clear();
+    if (s->stop && s->pending.empty()) {
+      bool busy = false;
+      for (int b : s->stream_busy) busy |= (b != 0);
+      if (!busy) break;
+      continue;
+    }
+    // admission, oldest first; a request that does not fit yet does not
+    // block younger ones (up to a bounded look-ahead)
+    std::vector<std::shared_ptr<Request>> batch;
+    size_t batch_keys = 0;
+    int looked = 0;
+    for (auto it = s->pending.begin(); it != s->pending.end() && looked < 256; ++looked) {
+      auto r = s->reqs[*it];
+      if (batchable(s, r->req)) {
+        const bool same_bits = batch.empty() || (batch[0]->req.begin_bit == r->req.begin_bit &&
+                                                 batch[0]->req.end_bit == r->req.end_bit);
+        if (same_bits && batch_keys + r->req.n <= s->max_batch_keys) {
+          batch.push_back(r);
+          batch_keys += r->req.n;
+          it = s->pending.erase(it);
+          continue;
+        }
+        ++it;
+        continue;
+      }
+      const int si = free_stream(s);
+      if (si < 0) break;
+      size_t off = 0;
+      const size_t need = single_footprint(r->req);
+      if (!s->pool->alloc(need, &off)) {
+        ++it;
+        continue;
+      }
+      Unit* u = new Unit;
+      u->srv = s;
+      u->members.push_back(r);
+      u->pool_off = off;
+      u->pool_bytes = rs::align_up(std::max<size_t>(need, 256), 256);
+      u->stream = si;
+      u->h_status = s->status_slab + si;
+      *u->h_status = 0u;
+      s->stream_busy[si] = 1;
+      r->state = 1;
+      it = s->pending.erase(it);
+      lk.unlock();
+      const rs_status st = launch_single(s, u);
+      lk.lock();
+      if (st != RS_OK) finish_unit(s, u, st);
+    }
+    if (!batch.empty()) {
+      const int si = free_stream(s);
+      const BatchPlan b = plan_batch(batch_keys, batch.size());
+      size_t off = 0;
+      if (si < 0 || !s->pool->alloc(b.bytes, &off)) {
+        // no room yet: back to the front of the queue, in order
+        for (auto r = batch.rbegin(); r != batch.rend(); ++r) s->pending.push_front((*r)->id);
+      } else {
+        Unit* u = new Unit;
+        u->srv = s;
+        u->members = batch;
+        u->pool_off = off;
+        u->pool_bytes = rs::align_up(b.bytes, 256);
+        u->stream = si;
+        u->h_status = s->status_slab + si;
+        *u->h_status = 0u;
+        s->stream_busy[si] = 1;
+        for (auto& m : batch) m->state = 1;
+        s->batches += 1;
+        s->batched_requests += batch.size();
+        lk.unlock();
+        const rs_status st = launch_batch(s, u, b);
+        lk.lock();
+        if (st != RS_OK) finish_unit(s, u, st);
+      }
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+rs_status rs_server_create(size_t budget_bytes, int streams, rs_server** out) {
+  if (!out || budget_bytes < (1u << 20) || streams < 1 || streams > 64) return RS_ERR_INVALID;
+  *out = nullptr;
+  auto* s = new rs_server;
+  cudaGetDevice(&s->device);
+  s->budget = budget_bytes;
+  if (cudaMalloc(reinterpret_cast<void**>(&s->pool_base), budget_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    delete s;
+    return RS_ERR_NOMEM;
+  }
+  s->pool.reset(new Pool(budget_bytes));
+  if (cudaHostAlloc(reinterpret_cast<void**>(&s->status_slab), sizeof(uint32_t) * streams,
+                    cudaHostAllocDefault) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(s->pool_base);
+    delete s;
+    return RS_ERR_NOMEM;
+  }
+  s->streams.resize(streams);
+  s->stream_busy.assign(streams, 0);
+  for (auto& st : s->streams) {
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+      st = nullptr;
+      for (auto& t : s->streams)
+        if (t) cudaStreamDestroy(t);
+      cudaFree(s->pool_base);
+      cudaFreeHost(s->status_slab);
+      delete s;
+      return RS_ERR_CUDA;
+    }
+  }
+  s->sched = std::thread(scheduler, s);
+  *out = s;
+  return RS_OK;
+}
+
+rs_status rs_server_destroy(rs_server* s) {
+  if (!s) return RS_ERR_INVALID;
+  {
+    std::lock_guard<std::mutex> g(s->mu);
+    s->stop = true;
+    for (uint64_t id : s->pending) {  // never started: cancelled
+      auto it = s->reqs.find(id);
+      if (it != s->reqs.end()) {
+        it->second->state = 2;
+        it->second->status = RS_ERR_CANCELLED;
+      }
+    }
+    s->pending.clear();
+    s->changes += 1;
+  }
+  s->cv.notify_all();
+  if (s->sched.joinable()) s->sched.join();
+  for (auto& st : s->streams) cudaStreamDestroy(st);
+  cudaFree(s->pool_base);
+  cudaFreeHost(s->status_slab);
+  delete s;
+  return RS_OK;
+}
+
+rs_status rs_submit(rs_server* s, const rs_request* req, rs_handle* out) {
+  if (!s || !req || !out || !valid_request(*req)) return RS_ERR_INVALID;
+  const size_t need = batchable(s, *req) ? plan_batch(req->n, 1).bytes : single_footprint(*req);
+  if (need > s->budget) return RS_ERR_INVALID;  // could never be admitted
+  auto r = std::make_shared<Request>();
+  r->req = *req;
+  r->t_submit = now_s();
+  {
+    std::lock_guard<std::mutex> g(s->mu);
+    if (s->stop) return RS_ERR_BUSY;
+    if (s->pending.size() >= (1u << 20)) return RS_ERR_BUSY;
+    r->id = s->next_id++;
+    if (s->first_submit == 0) s->first_submit = r->t_submit;
+    s->reqs[r->id] = r;
+    s->pending.push_back(r->id);
+    s->changes += 1;
+    s->max_queue = std::max(s->max_queue, s->pending.size());
+    *out = r->id;
+  }
+  s->cv.notify_all();
+  return RS_OK;
+}
+
+rs_status rs_poll(rs_server* s, rs_handle h, int* done) {
+  if (!s || !done) return RS_ERR_INVALID;
+  std::lock_guard<std::mutex> g(s->mu);
+  auto it = s->reqs.find(h);
+  if (it == s->reqs.end()) return RS_ERR_NOT_FOUND;
+  *done = it->second->state == 2;
+  if (!*done) return RS_OK;
+  const rs_status st = it->second->status;
+  s->reqs.erase(it);  // a handle is retired once its completion is reported
+  return st;
+}
+
+rs_status rs_cancel(rs_server* s, rs_handle h) {
+  if (!s) return RS_ERR_INVALID;
+  std::lock_guard<std::mutex> g(s->mu);
+  auto it = s->reqs.find(h);
+  if (it == s->reqs.end()) return RS_ERR_NOT_FOUND;
+  if (it->second->state != 0) return RS_ERR_BUSY;  // already on the GPU
+  auto q = std::find(s->pending.begin(), s->pending.end(), h);
+  if (q != s->pending.end()) s->pending.erase(q);
+  it->second->state = 2;
+  it->second->status = RS_ERR_CANCELLED;
+  s->changes += 1;
+  return RS_OK;
+}
+
+rs_status rs_server_stats(rs_server* s, rs_server_stats_t* out) {
+  if (!s || !out) return RS_ERR_INVALID;
+  std::lock_guard<std::mutex> g(s->mu);
+  std::memset(out, 0, sizeof(*out));
+  out->completed = s->completed;
+  out->failed = s->failed;
+  out->keys = s->keys_done;
+  out->batches = s->batches;
+  out->batched_requests = s->batched_requests;
+  out->queued = s->pending.size();
+  out->max_queued = s->max_queue;
+  out->pool_peak_bytes = s->pool->peak();
+  out->pool_used_bytes = s->pool->used();
+  if (!s->latencies.empty()) {
+    std::vector<double> l = s->latencies;
+    std::sort(l.begin(), l.end());
+    auto pct = [&](double p) {
+      const size_t i = std::min(l.size() - 1, size_t(p * double(l.size() - 1) + 0.5));
+      return l[i] * 1e3;
+    };
+    out->p50_ms = pct(0.50);
+    out->p99_ms = pct(0.99);
+    out->max_ms = l.back() * 1e3;
+  }
+  const double span = s->last_done - s->first_submit;
+  out->wall_s = span > 0 ? span : 0;
+  out->gkeys_per_s = span > 0 ? double(s->keys_done) / span / 1e9 : 0;
+  return RS_OK;
+}
+
+rs_status rs_server_reset_stats(rs_server* s) {
+  if (!s) return RS_ERR_INVALID;
+  std::lock_guard<std::mutex> g(s->mu);
+  s->latencies.clear();
+  s->completed = s->failed = s->keys_done = s->batches = s->batched_requests = 0;
+  s->first_submit = s->last_done = 0;
+  s->max_queue = s->pending.size();
+  return RS_OK;
+}
+
+}  // extern "C"

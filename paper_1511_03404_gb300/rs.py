@@ -46,6 +46,23 @@ class rs_config(ctypes.Structure):
     _fields_ = [("radix_bits", ctypes.c_int), ("variant", ctypes.c_int)]
 
 
+class rs_request(ctypes.Structure):
+    _fields_ = [("key_bytes", ctypes.c_int), ("val_bytes", ctypes.c_int),
+                ("n", ctypes.c_size_t), ("begin_bit", ctypes.c_int), ("end_bit", ctypes.c_int),
+                ("h_keys", ctypes.c_void_p), ("h_vals", ctypes.c_void_p),
+                ("h_out_keys", ctypes.c_void_p), ("h_out_vals", ctypes.c_void_p)]
+
+
+class rs_server_stats_t(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64),
+                ("keys", ctypes.c_uint64), ("batches", ctypes.c_uint64),
+                ("batched_requests", ctypes.c_uint64), ("queued", ctypes.c_uint64),
+                ("max_queued", ctypes.c_uint64), ("pool_peak_bytes", ctypes.c_size_t),
+                ("pool_used_bytes", ctypes.c_size_t), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
+                ("wall_s", ctypes.c_double), ("gkeys_per_s", ctypes.c_double)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -67,6 +84,13 @@ _SIGS = {
     "rs_segmented_sort_pairs": ([_vp, _vp, _vp, _vp, _sz, _vp, _sz, _i, _i, _vp, _sz, _vp, _vp],
                                 _i),
     "rs_segmented_workspace_bytes": ([_sz, _sz, _i, _i, _vp], _i),
+    "rs_server_create": ([_sz, _i, _vp], _i),
+    "rs_server_destroy": ([_vp], _i),
+    "rs_submit": ([_vp, _vp, _vp], _i),
+    "rs_poll": ([_vp, ctypes.c_uint64, _vp], _i),
+    "rs_cancel": ([_vp, ctypes.c_uint64], _i),
+    "rs_server_stats": ([_vp, _vp], _i),
+    "rs_server_reset_stats": ([_vp], _i),
     "rs_profile_begin": ([_i], _i),
     "rs_profile_end": ([_vp, _vp, _vp], _i),
     "rs_debug_set": ([_i, ctypes.c_longlong], _i),
@@ -217,6 +241,42 @@ def rs_workspace_status(ws, stream):
     info = ctypes.c_uint32()
     st = load().rs_workspace_status(ws, stream, ctypes.byref(info))
     return st, info.value
+
+
+def rs_server_create(budget_bytes: int, streams: int):
+    out = ctypes.c_void_p()
+    st = load().rs_server_create(budget_bytes, streams, ctypes.byref(out))
+    return st, out.value
+
+
+def rs_server_destroy(server) -> int:
+    return load().rs_server_destroy(server)
+
+
+def rs_submit(server, req: rs_request):
+    h = ctypes.c_uint64()
+    st = load().rs_submit(server, ctypes.byref(req), ctypes.byref(h))
+    return st, h.value
+
+
+def rs_poll(server, handle: int):
+    done = ctypes.c_int()
+    st = load().rs_poll(server, handle, ctypes.byref(done))
+    return st, bool(done.value)
+
+
+def rs_cancel(server, handle: int) -> int:
+    return load().rs_cancel(server, handle)
+
+
+def rs_server_stats(server):
+    out = rs_server_stats_t()
+    st = load().rs_server_stats(server, ctypes.byref(out))
+    return st, {name: getattr(out, name) for name, _ in rs_server_stats_t._fields_}
+
+
+def rs_server_reset_stats(server) -> int:
+    return load().rs_server_reset_stats(server)
 
 
 def rs_profile_begin(capacity: int) -> int:

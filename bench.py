@@ -18,6 +18,7 @@ oracle (the slow, plain LSD counting sort) on bounded samples instead.
 from __future__ import annotations
 
 import argparse
+import faulthandler
 import hashlib
 import json
 import os
@@ -149,6 +150,21 @@ def cpu_oracle_rate(sample_n: int, dists=DISTS, budget_s: float = 12.0) -> dict:
                       f"{t_total:.1f} s"}
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest x over all ranks (the slowest rank's time), via one all-reduce."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, steps: int, n: int, max_ms: float) -> float:
+    """Keys sorted by all ranks / slowest rank's time, in Gkeys/s."""
+    return world * steps * n / (max_ms / 1e3) / 1e9
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -262,20 +278,17 @@ def run_ours(args):
     rs.check(st, "rs_profile_end")
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = sum(step_ms)
-    if pg:
-        t = torch.tensor([total_ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps * n / (total_ms / 1e3) / 1e9
+    total_ms = max_over_ranks(total_ms, pg, dev)
+    value = whole_job_rate(world, args.steps, n, total_ms)
 
     # end to end through the C ABI: pinned host -> device, sort, device -> host
     e2e = {"value": None, "ms_per_step": None, "h2d": 0, "d2h": 0}
+    stage(f"timed sorts done: {total_ms / args.steps:.3f} ms per sort")
     if not args.quick:
+        stage("end to end (host buffers)")
         e2e = e2e_rate(torch, rs, keys_h, vals_h, n, dev, ws, args, dists)
     if pg and not args.quick:
-        t = torch.tensor([e2e["ms_per_step"]], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e["value"] = world * n / (float(t.item()) / 1e3) / 1e9
+        e2e["value"] = whole_job_rate(world, 1, n, max_over_ranks(e2e["ms_per_step"], pg, dev))
 
     if rank != 0:
         if pg:
@@ -319,9 +332,12 @@ def run_ours(args):
         "kernel_source": src,
     }
     if not (args.no_extras or args.quick) and world == 1:
+        stage("segmented: batched vs plain")
         line["segmented"] = bench_segmented(torch, rs, dev, args.seg_scaled)
+        stage("serving: Poisson trace")
         line["serving"] = bench_serving(torch, rs, seconds=args.serve_seconds)
     if not (args.no_cpu_baseline or args.quick):
+        stage("cpu baseline (oracle)")
         line["cpu_baseline"] = cpu_oracle_rate(1 << 24)
         line["cpu_baseline"]["host"] = host_description()
     print(json.dumps(line), flush=True)
@@ -440,8 +456,7 @@ def bench_segmented(torch, rs, dev, scaled: bool, reps: int = 3) -> dict:
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-        graph.replay()
-        with torch.cuda.stream(stream):
+            graph.replay()  # on the current stream, which is `stream` here
             e1.record(stream)
         stream.synchronize()
         batched.append(e0.elapsed_time(e1))
@@ -571,7 +586,13 @@ def bench_serving(torch, rs, seconds: float = 10.0, rate: float = 5000.0,
             "latency": "submit -> completion callback, host pinned buffers in and out"}
 
 
+def stage(msg: str) -> None:
+    """Progress marker on stderr (stdout carries only the JSON line)."""
+    print(f"[bench] {msg}", file=sys.stderr, flush=True)
+
+
 def main(argv=None):
+    faulthandler.enable()
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=60)

@@ -493,29 +493,43 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
     s_out[pos[j]] = s_kin[slot0 + j * 32];
   }
 
-  // ---- decoupled look-back: sum the counts of the preceding tiles for my digit
+  // ---- decoupled look-back: sum the counts of the preceding tiles for my
+  // digit, nearest first, until an inclusive prefix.  The status words of a
+  // window of LB predecessors are loaded at once, so a walk over many tiles
+  // that only published their own counts (the first wave of CTAs starts
+  // together) costs one L2 round trip per LB tiles, not per tile.
   if (tid < RADIX) {
+    constexpr int LB = 16;
     uint32_t excl = 0u;
     bool gave_up = false;
     if (tile > 0u) {
       int32_t pred = int32_t(tile) - 1;
-      for (;;) {
+      bool done = false;
+      while (!done && !gave_up) {
         if (pred < 0) {  // only possible if the status words were not cleared
           report_error(ctrl, kDevIndex, tile);
           gave_up = true;
           break;
         }
-        const uint32_t* p = &t.status[size_t(pred) * RADIX + tid];
-        uint32_t sw = ld_relaxed(p);
-        if ((sw & kFlagMask) == 0u) sw = wait_status(p, ctrl, timeout_ns, tile);
-        const uint32_t f = sw & kFlagMask;
-        if (f == kFlagErr) {
-          gave_up = true;
-          break;
+        uint32_t w[LB];
+#pragma unroll
+        for (int i = 0; i < LB; ++i)
+          w[i] = (pred - i >= 0) ? ld_relaxed(&t.status[size_t(pred - i) * RADIX + tid]) : 0u;
+#pragma unroll
+        for (int i = 0; i < LB; ++i) {
+          if (done || gave_up || pred - i < 0) continue;
+          uint32_t sw = w[i];
+          if ((sw & kFlagMask) == 0u)
+            sw = wait_status(&t.status[size_t(pred - i) * RADIX + tid], ctrl, timeout_ns, tile);
+          const uint32_t f = sw & kFlagMask;
+          if (f == kFlagErr) {
+            gave_up = true;
+          } else {
+            excl += sw & kValueMask;
+            if (f == kFlagInc) done = true;
+          }
         }
-        excl += sw & kValueMask;
-        if (f == kFlagInc) break;
-        --pred;
+        pred -= LB;
       }
       if (!t.silent)
         st_relaxed(&t.status[size_t(tile) * RADIX + tid],

@@ -317,31 +317,43 @@ void scheduler(rs_server* s) {
       if (!busy) break;
       continue;
     }
-    // admission, oldest first; a request that does not fit yet does not
-    // block younger ones (up to a bounded look-ahead)
+    // Admission, oldest first; a request that does not fit yet does not block
+    // younger ones (bounded look-ahead).  Every decision is taken under the
+    // lock and no iterator into the queue survives it: rs_submit may append
+    // to the queue as soon as the lock is released.
+    struct Launch {
+      Unit* u;
+      bool batch;
+      BatchPlan plan;
+    };
+    std::vector<Launch> launches;
     std::vector<std::shared_ptr<Request>> batch;
     size_t batch_keys = 0;
+    std::vector<uint64_t> keep;  // looked at, still queued, in order
     int looked = 0;
-    for (auto it = s->pending.begin(); it != s->pending.end() && looked < 256; ++looked) {
-      auto r = s->reqs[*it];
+    while (!s->pending.empty() && looked < 256) {
+      const uint64_t id = s->pending.front();
+      s->pending.pop_front();
+      auto found = s->reqs.find(id);
+      if (found == s->reqs.end()) continue;
+      ++looked;
+      std::shared_ptr<Request> r = found->second;
       if (batchable(s, r->req)) {
         const bool same_bits = batch.empty() || (batch[0]->req.begin_bit == r->req.begin_bit &&
                                                  batch[0]->req.end_bit == r->req.end_bit);
         if (same_bits && batch_keys + r->req.n <= s->max_batch_keys) {
           batch.push_back(r);
           batch_keys += r->req.n;
-          it = s->pending.erase(it);
-          continue;
+        } else {
+          keep.push_back(id);
         }
-        ++it;
         continue;
       }
       const int si = free_stream(s);
-      if (si < 0) break;
       size_t off = 0;
       const size_t need = single_footprint(r->req);
-      if (!s->pool->alloc(need, &off)) {
-        ++it;
+      if (si < 0 || !s->pool->alloc(need, &off)) {
+        keep.push_back(id);
         continue;
       }
       Unit* u = new Unit;
@@ -354,19 +366,14 @@ void scheduler(rs_server* s) {
       *u->h_status = 0u;
       s->stream_busy[si] = 1;
       r->state = 1;
-      it = s->pending.erase(it);
-      lk.unlock();
-      const rs_status st = launch_single(s, u);
-      lk.lock();
-      if (st != RS_OK) finish_unit(s, u, st);
+      launches.push_back(Launch{u, false, BatchPlan{}});
     }
     if (!batch.empty()) {
       const int si = free_stream(s);
       const BatchPlan b = plan_batch(batch_keys, batch.size());
       size_t off = 0;
       if (si < 0 || !s->pool->alloc(b.bytes, &off)) {
-        // no room yet: back to the front of the queue, in order
-        for (auto r = batch.rbegin(); r != batch.rend(); ++r) s->pending.push_front((*r)->id);
+        for (auto& m : batch) keep.push_back(m->id);  // no room yet
       } else {
         Unit* u = new Unit;
         u->srv = s;
@@ -380,12 +387,21 @@ void scheduler(rs_server* s) {
         for (auto& m : batch) m->state = 1;
         s->batches += 1;
         s->batched_requests += batch.size();
-        lk.unlock();
-        const rs_status st = launch_batch(s, u, b);
-        lk.lock();
-        if (st != RS_OK) finish_unit(s, u, st);
+        launches.push_back(Launch{u, true, b});
       }
     }
+    if (keep.size() > 1)
+      std::sort(keep.begin(), keep.end());  // ids grow with submission order
+    for (auto it = keep.rbegin(); it != keep.rend(); ++it) s->pending.push_front(*it);
+    if (launches.empty()) continue;
+    lk.unlock();
+    std::vector<rs_status> res(launches.size());
+    for (size_t i = 0; i < launches.size(); ++i)
+      res[i] = launches[i].batch ? launch_batch(s, launches[i].u, launches[i].plan)
+                                 : launch_single(s, launches[i].u);
+    lk.lock();
+    for (size_t i = 0; i < launches.size(); ++i)
+      if (res[i] != RS_OK) finish_unit(s, launches[i].u, res[i]);
   }
 }
 

@@ -147,7 +147,7 @@ rs_status rs_sort_pairs_u64(uint64_t* keys, uint64_t* vals, uint64_t* keys_alt,
  * running inside a framework that owns every device byte through its own
  * pool, real-time or callback contexts where an allocation could block or
  * synchronize the device, and systems whose memory must all be reserved at
- * start-up.  The scratch it needs (about 8 MiB) is a fixed array of device
+ * start-up.  The scratch it needs (9 MiB) is a fixed array of device
  * memory inside this library, present on every GPU that loads the library
  * until the process exits.
  *   keys, keys_alt, n, begin_bit, end_bit, stream, result_in_alt: as for
@@ -321,9 +321,12 @@ rs_status rs_profile_end(int* launches, double* ms, double* bytes);
 /* ---- fault injection for tests (host-set, off by default) ---- */
 
 typedef enum rs_debug_knob {
-  RS_DEBUG_TIMEOUT_NS = 0,        /* look-back wait limit in ns (default 2e9) */
+  RS_DEBUG_TIMEOUT_NS = 0,        /* look-back wait limit in ns (default 1e9) */
   RS_DEBUG_DROP_PUBLISH_TILE = 1, /* tile that never publishes its look-back status; -1 off */
-  RS_DEBUG_DROP_PUBLISH_PASS = 2  /* pass in which that tile stays silent */
+  RS_DEBUG_DROP_PUBLISH_PASS = 2, /* pass in which that tile stays silent */
+  RS_DEBUG_TRACE_PTR = 3,         /* device u64 buffer [tiles][16] for onesweep phase data; 0 off */
+  RS_DEBUG_TRACE_TILES = 4,       /* number of tiles the trace buffer holds */
+  RS_DEBUG_TRACE_PASS = 5         /* the digit pass whose tiles are traced */
 } rs_debug_knob;
 
 /* Set a knob for later calls from any thread; returns RS_ERR_INVALID for an unknown knob. */

@@ -74,12 +74,18 @@ int prepare_kernel(const void* func, int threads, int smem_bytes) {
 static std::atomic<long long> g_timeout_ns{1000000000LL};
 static std::atomic<long long> g_drop_tile{-1};
 static std::atomic<long long> g_drop_pass{-1};
+static std::atomic<long long> g_trace_ptr{0};
+static std::atomic<long long> g_trace_tiles{0};
+static std::atomic<long long> g_trace_pass{0};
 
 Knobs knobs_now() {
   Knobs k;
   k.timeout_ns = uint64_t(g_timeout_ns.load());
   k.drop_tile = int32_t(g_drop_tile.load());
   k.drop_pass = int32_t(g_drop_pass.load());
+  k.trace = reinterpret_cast<uint64_t*>(g_trace_ptr.load());
+  k.trace_tiles = uint32_t(g_trace_tiles.load());
+  k.trace_pass = int32_t(g_trace_pass.load());
   return k;
 }
 
@@ -401,6 +407,16 @@ rs_status rs_debug_set(rs_debug_knob knob, long long value) {
       return RS_OK;
     case RS_DEBUG_DROP_PUBLISH_PASS:
       g_drop_pass.store(value);
+      return RS_OK;
+    case RS_DEBUG_TRACE_PTR:
+      g_trace_ptr.store(value);
+      return RS_OK;
+    case RS_DEBUG_TRACE_TILES:
+      if (value < 0 || value > (1ll << 30)) return RS_ERR_INVALID;
+      g_trace_tiles.store(value);
+      return RS_OK;
+    case RS_DEBUG_TRACE_PASS:
+      g_trace_pass.store(value);
       return RS_OK;
   }
   return RS_ERR_INVALID;

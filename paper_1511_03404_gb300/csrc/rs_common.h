@@ -17,6 +17,14 @@ constexpr uint32_t kValueMask = (1u << kFlagShift) - 1u;
 
 constexpr int kMaxPasses = 16;  // 64-bit keys at 4-bit digits
 
+// Look-back groups: every kGroupTiles consecutive tiles of a pass also sum
+// their digit counts into one group word per digit (count in the low 24 bits,
+// number of tiles that added in the high 8), and the group's last tile
+// publishes the inclusive prefix through the group's end.
+constexpr int kGroupTiles = 32;
+constexpr uint32_t kGroupOne = 1u << 24;
+constexpr uint32_t kGroupCountMask = kGroupOne - 1u;
+
 // Device status codes (the values of rs_status).
 constexpr uint32_t kDevOk = 0;
 constexpr uint32_t kDevTimeout = 4;
@@ -38,6 +46,9 @@ struct Knobs {
   uint64_t timeout_ns;     // a look-back wait gives up after this long
   int32_t drop_tile;       // this tile never publishes its status (-1: off)
   int32_t drop_pass;       // ... in this pass
+  uint64_t* trace;         // device [trace_tiles][16] phase timestamps (ns) and counters, or null
+  uint32_t trace_tiles;    // tiles 0 .. trace_tiles-1 of trace_pass are recorded
+  int32_t trace_pass;
 };
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -47,18 +58,26 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 //   [0, 256)            Ctrl
 //   counts   u32 [passes][radix]    digit histograms (atomics; zeroed per call)
 //   offsets  u32 [passes][radix]    exclusive scans of the histograms
-//   status   u32 [passes][tiles][radix]  look-back words (zeroed by the upsweep)
+//   status   u32 [passes][tiles][radix]   look-back words of the tiles
+//   gagg     u32 [passes][groups][radix]  group digit counts (+ tiles added)
+//   ginc     u32 [passes][groups][radix]  group inclusive prefixes
+// status, gagg and ginc are one range, zeroed by the upsweep.
 struct Layout {
-  size_t counts, offsets, status, status_bytes, total, memset_bytes;
+  size_t counts, offsets, status, gagg, ginc, status_bytes, total, memset_bytes;
+  size_t tiles, groups;
 };
 
 inline Layout onesweep_layout(int passes, int radix_bits, size_t tiles) {
   Layout L;
   const size_t radix = size_t(1) << radix_bits;
+  L.tiles = tiles;
+  L.groups = (tiles + kGroupTiles - 1) / kGroupTiles;
   L.counts = 256;
   L.offsets = align_up(L.counts + size_t(passes) * radix * 4, 256);
   L.status = align_up(L.offsets + size_t(passes) * radix * 4, 256);
-  L.status_bytes = align_up(size_t(passes) * tiles * radix * 4, 256);
+  L.gagg = L.status + size_t(passes) * tiles * radix * 4;
+  L.ginc = L.gagg + size_t(passes) * L.groups * radix * 4;
+  L.status_bytes = align_up(L.ginc + size_t(passes) * L.groups * radix * 4 - L.status, 256);
   L.total = L.status + L.status_bytes;
   L.memset_bytes = L.offsets;  // Ctrl + counts
   return L;

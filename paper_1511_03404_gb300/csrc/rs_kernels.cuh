@@ -39,6 +39,15 @@ __device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
   return v;
 }
 
+__device__ __forceinline__ uint4 ld_relaxed_v4(const uint32_t* p) {
+  uint4 v;
+  asm volatile("ld.relaxed.gpu.global.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p)
+               : "memory");
+  return v;
+}
+
 __device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
   asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
@@ -53,6 +62,37 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
   uint32_t m;
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
   return m;
+}
+
+// Stable rank of ITEMS digits per lane inside one warp.  Item j of lane l
+// comes after item j' < j of every lane and after item j of lanes < l.
+// The lanes holding the same digit (the "peers") are found with one shared
+// atomic OR of the lane bit into a per-warp word for that digit (mm, all zero
+// on entry and on exit): on sm_103a this sustains several times the rate of
+// match.any.  The warp's running count per digit (wh) is updated by the peer
+// group's highest lane; pos[j] receives the count of earlier equal digits.
+template <int ITEMS>
+__device__ __forceinline__ void warp_rank(const uint32_t (&dg)[ITEMS], uint32_t (&pos)[ITEMS],
+                                          uint32_t* wh, uint32_t* mm, int lane) {
+  const uint32_t bit = 1u << lane;
+  const uint32_t lt = bit - 1u;
+#pragma unroll
+  for (int j = 0; j < ITEMS; ++j) {
+    const uint32_t d = dg[j];
+    atomicOr(&mm[d], bit);
+    __syncwarp();
+    const uint32_t peers = mm[d];
+    __syncwarp();
+    const int leader = 31 - __clz(peers);
+    uint32_t before = 0u;
+    if (lane == leader) {
+      mm[d] = 0u;
+      before = wh[d];
+      wh[d] = before + uint32_t(__popc(peers));
+    }
+    __syncwarp();
+    pos[j] = __shfl_sync(kFull, before, leader) + uint32_t(__popc(peers & lt));
+  }
 }
 
 template <class K>
@@ -248,7 +288,8 @@ struct OnesweepSmem {
   static constexpr int TILE = THREADS * ITEMS;
   static constexpr int ELEM = (int(sizeof(K)) > VB) ? int(sizeof(K)) : VB;
   static constexpr int WH = 0;                              // u32 [WARPS][RADIX]
-  static constexpr int CNT = WH + WARPS * RADIX * 4;       // u32 [RADIX] tile counts
+  static constexpr int MM = WH + WARPS * RADIX * 4;        // u32 [WARPS][RADIX] peer masks
+  static constexpr int CNT = MM + WARPS * RADIX * 4;       // u32 [RADIX] tile counts
   static constexpr int TSTART = CNT + RADIX * 4;           // u32 [RADIX] tile digit starts
   static constexpr int GBASE = TSTART + RADIX * 4;         // u32 [RADIX] global base
   static constexpr int TOT = GBASE + RADIX * 4;            // u32 [32]
@@ -272,8 +313,87 @@ struct TileArgs {
   uint32_t shift, mask;         // digit of this pass: (key >> shift) & mask
   const uint32_t* pass_offsets; // [RADIX] global digit offsets of this pass
   uint32_t* status;             // [tiles][RADIX] look-back words of this array and pass
+  uint32_t* gagg;               // [groups][RADIX] group counts of this pass, or null (flat walk)
+  uint32_t* ginc;               // [groups][RADIX] group inclusive prefixes of this pass
+  uint32_t tiles;               // tiles of this array
   bool silent;                  // test-only: publish nothing for this tile
+  uint64_t* trace;              // test-only: 16 phase stamps / counters of this tile, or null
 };
+
+__device__ __forceinline__ uint32_t sm_id() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%smid;" : "=r"(r));
+  return r;
+}
+
+// test-only phase stamp (thread 0)
+__device__ __forceinline__ void stamp(uint64_t* tr, int k) {
+  if (tr != nullptr && threadIdx.x == 0) tr[k] = global_ns();
+}
+
+// ---- look-back walks (one thread per digit)
+
+// Bounded wait until a group word reports `need` contributing tiles.
+static __device__ __noinline__ uint32_t wait_group(const uint32_t* p, uint32_t need, Ctrl* ctrl,
+                                                   uint64_t timeout_ns, uint32_t tile, bool* ok) {
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 1;; ++it) {
+    const uint32_t w = ld_relaxed(p);
+    if ((w >> 24) >= need) {
+      *ok = true;
+      return w;
+    }
+    if ((it & 63u) == 0u) {
+      if (ld_relaxed(&ctrl->error) != 0u) break;
+      if (global_ns() - t0 > timeout_ns) {
+        report_error(ctrl, kDevTimeout, tile);
+        break;
+      }
+    }
+  }
+  *ok = false;
+  return 0u;
+}
+
+// test-only counters of digit 0's look-back (thread 0)
+__device__ __forceinline__ void trace_add(uint64_t* tr, int k, uint64_t v) {
+  if (tr != nullptr && threadIdx.x == 0) tr[k] += v;
+}
+
+// Walk the tiles from, from-1, ..., lo of one digit, nearest first, adding
+// their published counts to excl until an inclusive prefix (done).  A window
+// of LB status words is loaded at once; each load is coalesced across the
+// warp (consecutive digits of a tile are consecutive words).
+template <int RADIX, int LB>
+__device__ __forceinline__ void walk_tiles(const uint32_t* status, int d, int32_t from, int32_t lo,
+                                           uint32_t& excl, bool& done, bool& gave_up, Ctrl* ctrl,
+                                           uint64_t timeout_ns, uint32_t tile, uint64_t* tr) {
+  int32_t pred = from;
+  while (!done && !gave_up && pred >= lo) {
+    trace_add(tr, 10, 1);
+    uint32_t w[LB];
+#pragma unroll
+    for (int i = 0; i < LB; ++i)
+      w[i] = (pred - i >= lo) ? ld_relaxed(&status[size_t(pred - i) * RADIX + d]) : 0u;
+#pragma unroll
+    for (int i = 0; i < LB; ++i) {
+      if (done || gave_up || pred - i < lo) continue;
+      uint32_t sw = w[i];
+      if ((sw & kFlagMask) == 0u) {
+        trace_add(tr, 12, 1);
+        sw = wait_status(&status[size_t(pred - i) * RADIX + d], ctrl, timeout_ns, tile);
+      }
+      const uint32_t f = sw & kFlagMask;
+      if (f == kFlagErr) {
+        gave_up = true;
+      } else {
+        excl += sw & kValueMask;
+        if (f == kFlagInc) done = true;
+      }
+    }
+    pred -= LB;
+  }
+}
 
 // ---- bulk (TMA engine) copies global -> shared, completed on an mbarrier
 
@@ -393,6 +513,8 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
   const uint32_t tile = t.tile, n = t.n;
   const uint32_t tile_base = tile * uint32_t(TILE);
   const uint32_t tile_len = min(uint32_t(TILE), n - tile_base);
+  stamp(t.trace, 0);
+  if (t.trace != nullptr && tid == 0) t.trace[7] = sm_id();
 
   if (tid == 0) {
     mbar_init(s_bar);
@@ -430,37 +552,24 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
   // past the end: the largest digit, so these items rank after every key of
   // the tile and are never written out
   for (uint32_t i = tile_len + tid; i < uint32_t(TILE); i += THREADS) s_kin[i] = ~K(0);
-  for (int i = tid; i < WARPS * RADIX; i += THREADS) s_wh[i] = 0u;
+  for (int i = tid; i < 2 * WARPS * RADIX; i += THREADS) s_wh[i] = 0u;  // counters + masks
   bool landed = mbar_wait_bounded(s_bar, 0u, ctrl, timeout_ns, tile);
   if (!landed) landed = mbar_wait_bounded(s_bar, 0u, ctrl, timeout_ns, tile);
   const int any_late = __syncthreads_or(!landed);
   if (tid == 0) mbar_inval(s_bar);  // its memory may serve other work items later
   if (any_late) return false;       // CTA-uniform
+  stamp(t.trace, 1);
 
   // ---- rank within the warp: warp w owns tile slots [w*ITEMS*32, (w+1)*ITEMS*32),
-  // item j of lane l is slot w*ITEMS*32 + j*32 + l.  Peers with the same digit
-  // come from match.any; the warp's running count per digit is in its private
-  // shared counters.  The three loops are independent across items, so the
-  // latencies of the match, the atomic and the shuffle overlap.
+  // item j of lane l is slot w*ITEMS*32 + j*32 + l
   const uint32_t slot0 = uint32_t(warp * ITEMS * 32 + lane);
-  uint32_t dg[ITEMS], peers[ITEMS], pos[ITEMS];
+  uint32_t dg[ITEMS], pos[ITEMS];
 #pragma unroll
   for (int j = 0; j < ITEMS; ++j) dg[j] = digit_of(s_kin[slot0 + j * 32], t.shift, t.mask);
-#pragma unroll
-  for (int j = 0; j < ITEMS; ++j) peers[j] = __match_any_sync(kFull, dg[j]);
-  {
-    uint32_t* wh = s_wh + warp * RADIX;
-#pragma unroll
-    for (int j = 0; j < ITEMS; ++j) {
-      pos[j] = 0u;
-      if (lane == 31 - __clz(peers[j])) pos[j] = atomicAdd(&wh[dg[j]], uint32_t(__popc(peers[j])));
-    }
-    const uint32_t lt = lanemask_lt();
-#pragma unroll
-    for (int j = 0; j < ITEMS; ++j)
-      pos[j] = __shfl_sync(kFull, pos[j], 31 - __clz(peers[j])) + uint32_t(__popc(peers[j] & lt));
-  }
+  warp_rank<ITEMS>(dg, pos, s_wh + warp * RADIX,
+                   reinterpret_cast<uint32_t*>(smem + S::MM) + warp * RADIX, lane);
   __syncthreads();
+  stamp(t.trace, 2);
 
   // ---- per digit: exclusive prefix over warps, tile count, publish the count
   uint32_t my_cnt = 0u;
@@ -473,8 +582,11 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
       run += c;
     }
     my_cnt = run;
-    if (!t.silent)
+    if (!t.silent) {
       st_relaxed(&t.status[size_t(tile) * RADIX + tid], (tile == 0u ? kFlagInc : kFlagAgg) | run);
+      if (t.gagg != nullptr)
+        atomicAdd(&t.gagg[size_t(tile / kGroupTiles) * RADIX + tid], run | kGroupOne);
+    }
   }
   const uint32_t my_start = block_exclusive_scan<THREADS>(my_cnt, s_tot);
   if (tid < RADIX) {
@@ -484,6 +596,7 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
   __syncthreads();
   for (int i = tid; i < WARPS * RADIX; i += THREADS) s_wh[i] += s_tstart[i & (RADIX - 1)];
   __syncthreads();
+  stamp(t.trace, 3);
 
   // ---- keys into the stage in (digit, input) order
   K* s_out = reinterpret_cast<K*>(smem + S::OUT);
@@ -492,54 +605,79 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
     pos[j] += s_wh[warp * RADIX + dg[j]];
     s_out[pos[j]] = s_kin[slot0 + j * 32];
   }
+  stamp(t.trace, 8);
 
-  // ---- decoupled look-back: sum the counts of the preceding tiles for my
-  // digit, nearest first, until an inclusive prefix.  The status words of a
-  // window of LB predecessors are loaded at once, so a walk over many tiles
-  // that only published their own counts (the first wave of CTAs starts
-  // together) costs one L2 round trip per LB tiles, not per tile.
+  // ---- decoupled look-back: the sum of the counts of the preceding tiles for
+  // my digit.  With groups: the earlier tiles of my group (at most one window),
+  // then earlier groups nearest first, 16 per L2 round trip, each giving
+  // either its inclusive prefix (stop) or its complete count (go on).  The
+  // walk then no longer grows with the number of tiles in flight.
   if (tid < RADIX) {
-    constexpr int LB = 16;
     uint32_t excl = 0u;
     bool gave_up = false;
     if (tile > 0u) {
-      int32_t pred = int32_t(tile) - 1;
       bool done = false;
-      while (!done && !gave_up) {
-        if (pred < 0) {  // only possible if the status words were not cleared
+      if (t.gagg == nullptr) {
+        walk_tiles<RADIX, 32>(t.status, tid, int32_t(tile) - 1, 0, excl, done, gave_up, ctrl,
+                              timeout_ns, tile, t.trace);
+        if (!done && !gave_up) {  // tile 0 is inclusive: only if words were not cleared
           report_error(ctrl, kDevIndex, tile);
           gave_up = true;
-          break;
         }
-        uint32_t w[LB];
+      } else {
+        const int32_t g = int32_t(tile / kGroupTiles);
+        walk_tiles<RADIX, 32>(t.status, tid, int32_t(tile) - 1, g * kGroupTiles, excl, done,
+                              gave_up, ctrl, timeout_ns, tile, t.trace);
+        for (int32_t h = g - 1; !done && !gave_up && h >= 0; h -= 16) {
+          trace_add(t.trace, 11, 1);
+          uint32_t wi[16], wa[16];
 #pragma unroll
-        for (int i = 0; i < LB; ++i)
-          w[i] = (pred - i >= 0) ? ld_relaxed(&t.status[size_t(pred - i) * RADIX + tid]) : 0u;
+          for (int q = 0; q < 16; ++q) {
+            wi[q] = (h - q >= 0) ? ld_relaxed(&t.ginc[size_t(h - q) * RADIX + tid]) : 0u;
+            wa[q] = (h - q >= 0) ? ld_relaxed(&t.gagg[size_t(h - q) * RADIX + tid]) : 0u;
+          }
 #pragma unroll
-        for (int i = 0; i < LB; ++i) {
-          if (done || gave_up || pred - i < 0) continue;
-          uint32_t sw = w[i];
-          if ((sw & kFlagMask) == 0u)
-            sw = wait_status(&t.status[size_t(pred - i) * RADIX + tid], ctrl, timeout_ns, tile);
-          const uint32_t f = sw & kFlagMask;
-          if (f == kFlagErr) {
-            gave_up = true;
-          } else {
-            excl += sw & kValueMask;
-            if (f == kFlagInc) done = true;
+          for (int q = 0; q < 16; ++q) {
+            const int32_t hh = h - q;
+            if (done || gave_up || hh < 0) continue;
+            const uint32_t fi = wi[q] & kFlagMask;
+            if (fi == kFlagErr) {
+              gave_up = true;
+            } else if (fi == kFlagInc) {
+              excl += wi[q] & kValueMask;
+              done = true;
+            } else {
+              const uint32_t need = min(uint32_t(kGroupTiles), t.tiles - uint32_t(hh) * kGroupTiles);
+              uint32_t ag = wa[q];
+              if ((ag >> 24) < need) {
+                trace_add(t.trace, 13, 1);
+                bool ok = false;
+                ag = wait_group(&t.gagg[size_t(hh) * RADIX + tid], need, ctrl, timeout_ns, tile,
+                                &ok);
+                if (!ok) gave_up = true;
+              }
+              if (!gave_up) excl += ag & kGroupCountMask;
+            }
           }
         }
-        pred -= LB;
+        // a walk that ran past group 0 without an inclusive prefix has summed
+        // every earlier group completely
       }
       if (!t.silent)
         st_relaxed(&t.status[size_t(tile) * RADIX + tid],
                    gave_up ? kFlagErr : (kFlagInc | ((excl + my_cnt) & kValueMask)));
     }
+    if (t.ginc != nullptr && !t.silent &&
+        ((tile + 1) % kGroupTiles == 0 || tile + 1 == t.tiles))
+      st_relaxed(&t.ginc[size_t(tile / kGroupTiles) * RADIX + tid],
+                 gave_up ? kFlagErr : (kFlagInc | ((excl + my_cnt) & kValueMask)));
     if (gave_up) s_misc[1] = 1u;
+    stamp(t.trace, 9);
     s_gbase[tid] = t.pass_offsets[tid] + excl - my_start;
   }
   __syncthreads();
   if (s_misc[1]) return false;  // the output of this call is void; ctrl->error says why
+  stamp(t.trace, 4);
 
   // ---- scatter: consecutive threads take consecutive stage slots, which map
   // to consecutive output addresses inside each digit run
@@ -559,6 +697,7 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
       }
     }
   }
+  stamp(t.trace, 5);
   if constexpr (VB > 0) {
     __syncthreads();
     V* s_vout = reinterpret_cast<V*>(smem + S::OUT);
@@ -571,6 +710,7 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
       if (gidx[s] != 0xffffffffu) t.vdst[gidx[s]] = s_vout[i];
     }
   }
+  stamp(t.trace, 6);
   return true;
 }
 
@@ -582,6 +722,7 @@ __global__ void __launch_bounds__(THREADS, MINB)
     k_onesweep(K* __restrict__ k0, K* __restrict__ k1, ValT<VB>* __restrict__ v0,
                ValT<VB>* __restrict__ v1, uint32_t n, int pass, uint32_t shift, uint32_t mask,
                const uint32_t* __restrict__ pass_offsets, uint32_t* __restrict__ status,
+               uint32_t* __restrict__ gagg, uint32_t* __restrict__ ginc, uint32_t tiles,
                Ctrl* __restrict__ ctrl, Knobs knobs) {
   using S = OnesweepSmem<K, VB, RADIX_BITS, THREADS, ITEMS>;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -607,7 +748,13 @@ __global__ void __launch_bounds__(THREADS, MINB)
   t.mask = mask;
   t.pass_offsets = pass_offsets;
   t.status = status;
+  t.gagg = gagg;
+  t.ginc = ginc;
+  t.tiles = tiles;
   t.silent = (int(t.tile) == knobs.drop_tile) && (pass == knobs.drop_pass);
+  t.trace = (knobs.trace != nullptr && pass == knobs.trace_pass && t.tile < knobs.trace_tiles)
+                ? knobs.trace + size_t(t.tile) * 16
+                : nullptr;
   onesweep_tile<K, VB, RADIX_BITS, THREADS, ITEMS, false>(t, ctrl, knobs.timeout_ns, smem);
 }
 
@@ -620,7 +767,8 @@ struct SmallSmem {
   static constexpr int TILE = THREADS * ITEMS;
   static constexpr int ELEM = (int(sizeof(K)) > VB) ? int(sizeof(K)) : VB;
   static constexpr int WH = 0;                      // u32 [WARPS][RADIX]
-  static constexpr int TOT = WH + WARPS * RADIX * 4; // u32 [32]
+  static constexpr int MM = WH + WARPS * RADIX * 4;  // u32 [WARPS][RADIX] peer masks
+  static constexpr int TOT = MM + WARPS * RADIX * 4; // u32 [32]
   static constexpr int STAGE = (TOT + 32 * 4 + 15) / 16 * 16;
   static constexpr int BYTES = STAGE + TILE * ELEM;
 };
@@ -650,24 +798,16 @@ __device__ __forceinline__ void cta_sort(const K* kin, const ValT<VB>* vin, K* k
     key[j] = i < len ? kin[i] : ~K(0);  // past the end: largest digit in every pass
     if constexpr (VB > 0) val[j] = i < len ? vin[i] : V(0);
   }
-  const uint32_t lt = lanemask_lt();
   for (int lo = begin_bit; lo < end_bit; lo += RADIX_BITS) {
     const uint32_t shift = uint32_t(lo);
     const uint32_t mask = (1u << (min(lo + RADIX_BITS, end_bit) - lo)) - 1u;
-    for (int i = tid; i < WARPS * RADIX; i += THREADS) s_wh[i] = 0u;
+    for (int i = tid; i < 2 * WARPS * RADIX; i += THREADS) s_wh[i] = 0u;  // counters + masks
     __syncthreads();
-    uint32_t pos[ITEMS];
-    uint32_t* wh = s_wh + warp * RADIX;
+    uint32_t pos[ITEMS], dg[ITEMS];
 #pragma unroll
-    for (int j = 0; j < ITEMS; ++j) {
-      const uint32_t d = digit_of(key[j], shift, mask);
-      const uint32_t peers = __match_any_sync(kFull, d);
-      const int leader = 31 - __clz(peers);
-      uint32_t before = 0u;
-      if (lane == leader) before = atomicAdd(&wh[d], uint32_t(__popc(peers)));
-      before = __shfl_sync(kFull, before, leader);
-      pos[j] = before + uint32_t(__popc(peers & lt));
-    }
+    for (int j = 0; j < ITEMS; ++j) dg[j] = digit_of(key[j], shift, mask);
+    warp_rank<ITEMS>(dg, pos, s_wh + warp * RADIX,
+                     reinterpret_cast<uint32_t*>(smem + S::MM) + warp * RADIX, lane);
     __syncthreads();
     uint32_t cnt = 0u;
     if (tid < RADIX) {

@@ -18,8 +18,9 @@
 namespace {
 
 // Workspace of a sort of up to RS_NOALLOC_MAX_N keys: control block, digit
-// counts and offsets, and one look-back word per (pass, tile, digit).
-constexpr size_t kScratchBytes = (size_t(8) << 20) + (size_t(16) << 10);
+// counts and offsets, one look-back word per (pass, tile, digit) and two per
+// (pass, group of tiles, digit): about 8.5 MiB at 2^23 keys.
+constexpr size_t kScratchBytes = size_t(9) << 20;
 
 __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 

@@ -363,7 +363,11 @@ __global__ void __launch_bounds__(THREADS, 2)
         t.mask = (1u << (min(lo + RADIX_BITS, a.end_bit) - lo)) - 1u;
         t.pass_offsets = a.offsets + (size_t(li) * passes + p) * RADIX;
         t.status = a.status + (size_t(p) * a.tiles_max + d.tile0) * RADIX;
+        t.gagg = nullptr;  // segments are short: flat walk
+        t.ginc = nullptr;
+        t.tiles = ntiles;
         t.silent = false;
+        t.trace = nullptr;
         onesweep_tile<K, VB, RADIX_BITS, THREADS, ITEMS, true>(t, ctrl, a.knobs.timeout_ns,
                                                                smem);
         __threadfence();

@@ -33,7 +33,8 @@ RS_KERNEL_UPSWEEP, RS_KERNEL_ONESWEEP, RS_KERNEL_SMALL, RS_KERNEL_SEGMENTED = ra
 RS_KERNEL_KINDS = 4
 KERNEL_NAMES = ("upsweep", "onesweep", "small", "segmented")
 
-RS_DEBUG_TIMEOUT_NS, RS_DEBUG_DROP_PUBLISH_TILE, RS_DEBUG_DROP_PUBLISH_PASS = range(3)
+(RS_DEBUG_TIMEOUT_NS, RS_DEBUG_DROP_PUBLISH_TILE, RS_DEBUG_DROP_PUBLISH_PASS, RS_DEBUG_TRACE_PTR,
+ RS_DEBUG_TRACE_TILES, RS_DEBUG_TRACE_PASS) = range(6)
 
 
 class RsError(RuntimeError):

@@ -66,11 +66,14 @@ def test_workspace_sizes():
     assert st == rs.RS_OK and b == 0
     st, b1 = rs.rs_workspace_bytes(4, 4, 2**26, 0, 32)
     assert st == rs.RS_OK
-    # onesweep: 256 B control + counts + offsets + look-back words of every pass
+    # onesweep: 256 B control + counts + offsets + look-back words of every
+    # pass (per tile, plus two per group of 32 tiles)
     info = rs.rs_variant_info(4, 4, 0)
     tiles = -(-2**26 // (info["threads"] * info["items"]))
-    assert b1 >= 4 * tiles * 256 * 4 + 2 * 4 * 256 * 4
-    assert b1 < 4 * tiles * 256 * 4 + 16384
+    groups = -(-tiles // 32)
+    words = 4 * (tiles + 2 * groups) * 256
+    assert b1 >= 4 * words + 2 * 4 * 256 * 4
+    assert b1 < 4 * words + 16384
     st, b2 = rs.rs_workspace_bytes(8, 0, 2**26, 0, 64)
     assert st == rs.RS_OK and b2 > b1
     assert rs.rs_workspace_bytes(4, 4, rs.RS_MAX_N + 1, 0, 32)[0] == rs.RS_ERR_INVALID

@@ -326,7 +326,8 @@ typedef enum rs_debug_knob {
   RS_DEBUG_DROP_PUBLISH_PASS = 2, /* pass in which that tile stays silent */
   RS_DEBUG_TRACE_PTR = 3,         /* device u64 buffer [tiles][16] for onesweep phase data; 0 off */
   RS_DEBUG_TRACE_TILES = 4,       /* number of tiles the trace buffer holds */
-  RS_DEBUG_TRACE_PASS = 5         /* the digit pass whose tiles are traced */
+  RS_DEBUG_TRACE_PASS = 5,        /* the digit pass whose tiles are traced */
+  RS_DEBUG_LB_SMALL = 6           /* look-back windows of 8 status words instead of 32 */
 } rs_debug_knob;
 
 /* Set a knob for later calls from any thread; returns RS_ERR_INVALID for an unknown knob. */

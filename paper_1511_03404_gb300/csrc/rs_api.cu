@@ -77,6 +77,7 @@ static std::atomic<long long> g_drop_pass{-1};
 static std::atomic<long long> g_trace_ptr{0};
 static std::atomic<long long> g_trace_tiles{0};
 static std::atomic<long long> g_trace_pass{0};
+static std::atomic<long long> g_lb_small{0};
 
 Knobs knobs_now() {
   Knobs k;
@@ -86,6 +87,7 @@ Knobs knobs_now() {
   k.trace = reinterpret_cast<uint64_t*>(g_trace_ptr.load());
   k.trace_tiles = uint32_t(g_trace_tiles.load());
   k.trace_pass = int32_t(g_trace_pass.load());
+  k.lb_small = int32_t(g_lb_small.load());
   return k;
 }
 
@@ -417,6 +419,9 @@ rs_status rs_debug_set(rs_debug_knob knob, long long value) {
       return RS_OK;
     case RS_DEBUG_TRACE_PASS:
       g_trace_pass.store(value);
+      return RS_OK;
+    case RS_DEBUG_LB_SMALL:
+      g_lb_small.store(value);
       return RS_OK;
   }
   return RS_ERR_INVALID;

@@ -49,19 +49,29 @@ struct Knobs {
   uint64_t* trace;         // device [trace_tiles][16] phase timestamps (ns) and counters, or null
   uint32_t trace_tiles;    // tiles 0 .. trace_tiles-1 of trace_pass are recorded
   int32_t trace_pass;
+  int32_t lb_small;        // test-only: look-back windows of 8 instead of 32 words
 };
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Word of (tile or group t, digit d) in a [t/4][radix][4] look-back array.
+template <int RADIX>
+__host__ __device__ __forceinline__ size_t lb_index(uint32_t t, uint32_t d) {
+  return ((size_t(t >> 2) * RADIX + d) << 2) | (t & 3u);
+}
 
 // Workspace of one onesweep sort with `passes` digit passes, radix 2^r and
 // `tiles` tiles per pass:
 //   [0, 256)            Ctrl
 //   counts   u32 [passes][radix]    digit histograms (atomics; zeroed per call)
 //   offsets  u32 [passes][radix]    exclusive scans of the histograms
-//   status   u32 [passes][tiles][radix]   look-back words of the tiles
-//   gagg     u32 [passes][groups][radix]  group digit counts (+ tiles added)
-//   ginc     u32 [passes][groups][radix]  group inclusive prefixes
-// status, gagg and ginc are one range, zeroed by the upsweep.
+//   status   u32 [passes][tiles/4][radix][4]   look-back words of the tiles
+//   gagg     u32 [passes][groups/4][radix][4]  group digit counts (+ tiles added)
+//   ginc     u32 [passes][groups/4][radix][4]  group inclusive prefixes
+// Four consecutive tiles (groups) of one digit are adjacent, so a look-back
+// thread fetches four of them with one 16-byte load, and a warp's loads (32
+// digits) are one contiguous 512-byte block.  status, gagg and ginc are one
+// range, zeroed by the upsweep; tile and group counts are rounded up to 4.
 struct Layout {
   size_t counts, offsets, status, gagg, ginc, status_bytes, total, memset_bytes;
   size_t tiles, groups;
@@ -70,12 +80,12 @@ struct Layout {
 inline Layout onesweep_layout(int passes, int radix_bits, size_t tiles) {
   Layout L;
   const size_t radix = size_t(1) << radix_bits;
-  L.tiles = tiles;
-  L.groups = (tiles + kGroupTiles - 1) / kGroupTiles;
+  L.tiles = align_up(tiles, 4);
+  L.groups = align_up((tiles + kGroupTiles - 1) / kGroupTiles, 4);
   L.counts = 256;
   L.offsets = align_up(L.counts + size_t(passes) * radix * 4, 256);
   L.status = align_up(L.offsets + size_t(passes) * radix * 4, 256);
-  L.gagg = L.status + size_t(passes) * tiles * radix * 4;
+  L.gagg = L.status + size_t(passes) * L.tiles * radix * 4;
   L.ginc = L.gagg + size_t(passes) * L.groups * radix * 4;
   L.status_bytes = align_up(L.ginc + size_t(passes) * L.groups * radix * 4 - L.status, 256);
   L.total = L.status + L.status_bytes;

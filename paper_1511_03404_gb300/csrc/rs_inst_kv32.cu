@@ -5,7 +5,7 @@ namespace rs {
 
 const Variant* variants_kv32(int* count) {
   static const Variant table[] = {
-      OnesweepSort<uint32_t, 4, 8, 256, 16, 3>::describe(),
+      OnesweepSort<uint32_t, 4, 8, 256, 16, 4>::describe(),
       SmallSort<uint32_t, 4, 8, 512, 16>::describe(),
   };
   *count = int(sizeof(table) / sizeof(table[0]));

@@ -287,18 +287,23 @@ struct OnesweepSmem {
   static constexpr int WARPS = THREADS / 32;
   static constexpr int TILE = THREADS * ITEMS;
   static constexpr int ELEM = (int(sizeof(K)) > VB) ? int(sizeof(K)) : VB;
-  static constexpr int WH = 0;                              // u32 [WARPS][RADIX]
-  static constexpr int MM = WH + WARPS * RADIX * 4;        // u32 [WARPS][RADIX] peer masks
-  static constexpr int CNT = MM + WARPS * RADIX * 4;       // u32 [RADIX] tile counts
+  static constexpr int WH = 0;                              // u32 [WARPS][RADIX] warp counters
+  static constexpr int CNT = WH + WARPS * RADIX * 4;       // u32 [RADIX] tile counts
   static constexpr int TSTART = CNT + RADIX * 4;           // u32 [RADIX] tile digit starts
   static constexpr int GBASE = TSTART + RADIX * 4;         // u32 [RADIX] global base
   static constexpr int TOT = GBASE + RADIX * 4;            // u32 [32]
   static constexpr int MISC = TOT + 32 * 4;                // u32 [4]: tile, abort, ...
-  static constexpr int MBAR = MISC + 16;                   // u64 mbarrier of the tile loads
-  static constexpr int KIN = (MBAR + 8 + 15) / 16 * 16;    // tile keys as loaded (+16 B skew)
-  static constexpr int VIN = KIN + TILE * int(sizeof(K)) + 16;  // tile values as loaded
-  static constexpr int OUT = VIN + (VB > 0 ? TILE * VB + 16 : 0);  // sorted stage
-  static constexpr int BYTES = OUT + TILE * ELEM;
+  static constexpr int MBAR = MISC + 16;                   // u64 [2] mbarriers: keys, values
+  // the tile's keys as loaded (+16 B skew); once they are staged in OUT, the
+  // tile's values are loaded here
+  static constexpr int KIN = (MBAR + 16 + 15) / 16 * 16;
+  // the tile in (digit, input) order: keys, then values; during the rank it
+  // holds the warps' peer masks (u32 [WARPS][RADIX])
+  static constexpr int OUT = KIN + TILE * ELEM + 16;
+  static constexpr int MM = OUT;
+  static constexpr int OUT_BYTES =
+      TILE * ELEM > WARPS * RADIX * 4 ? TILE * ELEM : WARPS * RADIX * 4;
+  static constexpr int BYTES = OUT + OUT_BYTES;
 };
 
 // Operands of one tile of one digit pass over one array (or one segment).
@@ -312,11 +317,13 @@ struct TileArgs {
   uint32_t tile;                // tile index inside the array / segment
   uint32_t shift, mask;         // digit of this pass: (key >> shift) & mask
   const uint32_t* pass_offsets; // [RADIX] global digit offsets of this pass
-  uint32_t* status;             // [tiles][RADIX] look-back words of this array and pass
-  uint32_t* gagg;               // [groups][RADIX] group counts of this pass, or null (flat walk)
-  uint32_t* ginc;               // [groups][RADIX] group inclusive prefixes of this pass
+  uint32_t* status;             // [tiles/4][RADIX][4] look-back words of this pass
+  uint32_t tile0;               // index of this array's tile 0 in status (a segment's first tile)
+  uint32_t* gagg;               // [groups/4][RADIX][4] group counts of this pass, or null (flat walk)
+  uint32_t* ginc;               // [groups/4][RADIX][4] group inclusive prefixes of this pass
   uint32_t tiles;               // tiles of this array
   bool silent;                  // test-only: publish nothing for this tile
+  bool lb_small;                // test-only: 8-word look-back windows
   uint64_t* trace;              // test-only: 16 phase stamps / counters of this tile, or null
 };
 
@@ -360,38 +367,48 @@ __device__ __forceinline__ void trace_add(uint64_t* tr, int k, uint64_t v) {
   if (tr != nullptr && threadIdx.x == 0) tr[k] += v;
 }
 
-// Walk the tiles from, from-1, ..., lo of one digit, nearest first, adding
-// their published counts to excl until an inclusive prefix (done).  A window
-// of LB status words is loaded at once; each load is coalesced across the
-// warp (consecutive digits of a tile are consecutive words).
-template <int RADIX, int LB>
-__device__ __forceinline__ void walk_tiles(const uint32_t* status, int d, int32_t from, int32_t lo,
-                                           uint32_t& excl, bool& done, bool& gave_up, Ctrl* ctrl,
-                                           uint64_t timeout_ns, uint32_t tile, uint64_t* tr) {
-  int32_t pred = from;
-  while (!done && !gave_up && pred >= lo) {
+// Walk the tiles from, from-1, ..., lo (indices into status) of one digit,
+// nearest first, adding their published counts to excl until an inclusive
+// prefix (done).  NB 16-byte L2 loads fetch a window of 4*NB tiles at once;
+// a warp's load is one contiguous 512-byte block (32 digits x 4 tiles).
+template <int RADIX, int NB>
+__device__ __forceinline__ void walk_tiles(const uint32_t* status, uint32_t d, int32_t from,
+                                           int32_t lo, uint32_t& excl, bool& done, bool& gave_up,
+                                           Ctrl* ctrl, uint64_t timeout_ns, uint32_t tile,
+                                           uint64_t* tr) {
+  int32_t hi = from;
+  while (!done && !gave_up && hi >= lo) {
     trace_add(tr, 10, 1);
-    uint32_t w[LB];
+    const int32_t b0 = hi >> 2;
+    uint4 v[NB];
 #pragma unroll
-    for (int i = 0; i < LB; ++i)
-      w[i] = (pred - i >= lo) ? ld_relaxed(&status[size_t(pred - i) * RADIX + d]) : 0u;
+    for (int k = 0; k < NB; ++k) {
+      const int32_t b = b0 - k;
+      v[k] = (4 * b + 3 >= lo)
+                 ? __ldcg(reinterpret_cast<const uint4*>(status + (size_t(b) * RADIX + d) * 4))
+                 : make_uint4(0u, 0u, 0u, 0u);
+    }
 #pragma unroll
-    for (int i = 0; i < LB; ++i) {
-      if (done || gave_up || pred - i < lo) continue;
-      uint32_t sw = w[i];
-      if ((sw & kFlagMask) == 0u) {
-        trace_add(tr, 12, 1);
-        sw = wait_status(&status[size_t(pred - i) * RADIX + d], ctrl, timeout_ns, tile);
-      }
-      const uint32_t f = sw & kFlagMask;
-      if (f == kFlagErr) {
-        gave_up = true;
-      } else {
-        excl += sw & kValueMask;
-        if (f == kFlagInc) done = true;
+    for (int k = 0; k < NB; ++k) {
+#pragma unroll
+      for (int c = 3; c >= 0; --c) {
+        const int32_t a = 4 * (b0 - k) + c;
+        if (done || gave_up || a > hi || a < lo) continue;
+        uint32_t sw = c == 0 ? v[k].x : c == 1 ? v[k].y : c == 2 ? v[k].z : v[k].w;
+        if ((sw & kFlagMask) == 0u) {
+          trace_add(tr, 12, 1);
+          sw = wait_status(status + lb_index<RADIX>(uint32_t(a), d), ctrl, timeout_ns, tile);
+        }
+        const uint32_t f = sw & kFlagMask;
+        if (f == kFlagErr) {
+          gave_up = true;
+        } else {
+          excl += sw & kValueMask;
+          if (f == kFlagInc) done = true;
+        }
       }
     }
-    pred -= LB;
+    hi = 4 * (b0 - NB + 1) - 1;
   }
 }
 
@@ -489,10 +506,12 @@ struct Stage {
   }
 };
 
-// One tile of one counting-sort pass (Sec. 2.6): stage the tile in shared
-// memory, rank it, publish its digit counts, look back, stable scatter.
-// Every thread of the CTA calls it.  Returns false (CTA-uniform) when a
-// bounded wait gave up, in which case nothing of this tile was written.
+// One tile of one counting-sort pass (Sec. 2.6): stage the tile's keys in
+// shared memory, rank them, publish the tile's digit counts, look back, and
+// scatter stably; the values are fetched into the freed key buffer while the
+// look-back and the key scatter run.  Every thread of the CTA calls it.
+// Returns false (CTA-uniform) when a bounded wait gave up, in which case
+// nothing of this tile was written and no copy into shared memory is pending.
 template <class K, int VB, int RADIX_BITS, int THREADS, int ITEMS, bool CG>
 __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ctrl,
                                               uint64_t timeout_ns, unsigned char* smem) {
@@ -507,7 +526,8 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
   uint32_t* s_gbase = reinterpret_cast<uint32_t*>(smem + S::GBASE);
   uint32_t* s_tot = reinterpret_cast<uint32_t*>(smem + S::TOT);
   uint32_t* s_misc = reinterpret_cast<uint32_t*>(smem + S::MISC);
-  uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem + S::MBAR);
+  uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem + S::MBAR);  // [0] keys, [1] values
+  uint32_t* s_mm = reinterpret_cast<uint32_t*>(smem + S::MM);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
   const uint32_t tile = t.tile, n = t.n;
@@ -517,47 +537,43 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
   if (t.trace != nullptr && tid == 0) t.trace[7] = sm_id();
 
   if (tid == 0) {
-    mbar_init(s_bar);
+    mbar_init(&s_bar[0]);
+    if constexpr (VB > 0) mbar_init(&s_bar[1]);
     s_misc[1] = 0u;
   }
   __syncthreads();
 
-  // ---- stage the tile (keys, values) in shared memory
+  // ---- stage the tile's keys
   const K* gk = t.ksrc + tile_base;
   const Stage<K> sk(gk, tile_len);
   K* s_kin = sk.at(smem + S::KIN);
-  V* s_vin = nullptr;
   if (tid == 0) {
-    uint32_t tx = sk.body;
-    if constexpr (VB > 0) tx += Stage<V>(t.vsrc + tile_base, tile_len).body;
     // shared memory this CTA used through ordinary loads and stores before
     // (an earlier work item) is about to be written by the copy engine; and,
     // when the source was written by other CTAs of this kernel, those stores
     // must be ordered before the copy engine reads them
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if constexpr (CG) asm volatile("fence.proxy.async.global;" ::: "memory");
-    mbar_arrive_expect_tx(s_bar, tx);
-    sk.issue(smem + S::KIN, gk, s_bar);
-    if constexpr (VB > 0) {
-      const Stage<V> sv(t.vsrc + tile_base, tile_len);
-      sv.issue(smem + S::VIN, t.vsrc + tile_base, s_bar);
-    }
+    mbar_arrive_expect_tx(&s_bar[0], sk.body);
+    sk.issue(smem + S::KIN, gk, &s_bar[0]);
   }
   sk.edges(smem + S::KIN, gk, tile_len);
-  if constexpr (VB > 0) {
-    const Stage<V> sv(t.vsrc + tile_base, tile_len);
-    s_vin = sv.at(smem + S::VIN);
-    sv.edges(smem + S::VIN, t.vsrc + tile_base, tile_len);
-  }
   // past the end: the largest digit, so these items rank after every key of
   // the tile and are never written out
   for (uint32_t i = tile_len + tid; i < uint32_t(TILE); i += THREADS) s_kin[i] = ~K(0);
-  for (int i = tid; i < 2 * WARPS * RADIX; i += THREADS) s_wh[i] = 0u;  // counters + masks
-  bool landed = mbar_wait_bounded(s_bar, 0u, ctrl, timeout_ns, tile);
-  if (!landed) landed = mbar_wait_bounded(s_bar, 0u, ctrl, timeout_ns, tile);
-  const int any_late = __syncthreads_or(!landed);
-  if (tid == 0) mbar_inval(s_bar);  // its memory may serve other work items later
-  if (any_late) return false;       // CTA-uniform
+  for (int i = tid; i < WARPS * RADIX; i += THREADS) {
+    s_wh[i] = 0u;
+    s_mm[i] = 0u;
+  }
+  bool landed = mbar_wait_bounded(&s_bar[0], 0u, ctrl, timeout_ns, tile);
+  if (!landed) landed = mbar_wait_bounded(&s_bar[0], 0u, ctrl, timeout_ns, tile);
+  if (__syncthreads_or(!landed)) {  // CTA-uniform
+    if (tid == 0) {
+      mbar_inval(&s_bar[0]);
+      if constexpr (VB > 0) mbar_inval(&s_bar[1]);
+    }
+    return false;
+  }
   stamp(t.trace, 1);
 
   // ---- rank within the warp: warp w owns tile slots [w*ITEMS*32, (w+1)*ITEMS*32),
@@ -566,8 +582,7 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
   uint32_t dg[ITEMS], pos[ITEMS];
 #pragma unroll
   for (int j = 0; j < ITEMS; ++j) dg[j] = digit_of(s_kin[slot0 + j * 32], t.shift, t.mask);
-  warp_rank<ITEMS>(dg, pos, s_wh + warp * RADIX,
-                   reinterpret_cast<uint32_t*>(smem + S::MM) + warp * RADIX, lane);
+  warp_rank<ITEMS>(dg, pos, s_wh + warp * RADIX, s_mm + warp * RADIX, lane);
   __syncthreads();
   stamp(t.trace, 2);
 
@@ -583,9 +598,10 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
     }
     my_cnt = run;
     if (!t.silent) {
-      st_relaxed(&t.status[size_t(tile) * RADIX + tid], (tile == 0u ? kFlagInc : kFlagAgg) | run);
+      st_relaxed(&t.status[lb_index<RADIX>(t.tile0 + tile, tid)],
+                 (tile == 0u ? kFlagInc : kFlagAgg) | run);
       if (t.gagg != nullptr)
-        atomicAdd(&t.gagg[size_t(tile / kGroupTiles) * RADIX + tid], run | kGroupOne);
+        atomicAdd(&t.gagg[lb_index<RADIX>(tile / kGroupTiles, tid)], run | kGroupOne);
     }
   }
   const uint32_t my_start = block_exclusive_scan<THREADS>(my_cnt, s_tot);
@@ -598,7 +614,7 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
   __syncthreads();
   stamp(t.trace, 3);
 
-  // ---- keys into the stage in (digit, input) order
+  // ---- keys into the stage in (digit, input) order (the peer masks are done)
   K* s_out = reinterpret_cast<K*>(smem + S::OUT);
 #pragma unroll
   for (int j = 0; j < ITEMS; ++j) {
@@ -607,76 +623,115 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
   }
   stamp(t.trace, 8);
 
+  // ---- the values into the key buffer, while the look-back and the key
+  // scatter run
+  V* s_vin = nullptr;
+  if constexpr (VB > 0) {
+    __syncthreads();  // every key has left the buffer
+    const V* gv = t.vsrc + tile_base;
+    const Stage<V> sv(gv, tile_len);
+    s_vin = sv.at(smem + S::KIN);
+    if (tid == 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive_expect_tx(&s_bar[1], sv.body);
+      sv.issue(smem + S::KIN, gv, &s_bar[1]);
+    }
+    sv.edges(smem + S::KIN, gv, tile_len);
+  }
+
   // ---- decoupled look-back: the sum of the counts of the preceding tiles for
-  // my digit.  With groups: the earlier tiles of my group (at most one window),
-  // then earlier groups nearest first, 16 per L2 round trip, each giving
-  // either its inclusive prefix (stop) or its complete count (go on).  The
-  // walk then no longer grows with the number of tiles in flight.
+  // my digit.  With groups: the earlier tiles of my group, then earlier
+  // groups nearest first, each giving either its inclusive prefix (stop) or
+  // its complete count (go on).  The walk then no longer grows with the
+  // number of tiles in flight.
   if (tid < RADIX) {
     uint32_t excl = 0u;
     bool gave_up = false;
     if (tile > 0u) {
       bool done = false;
       if (t.gagg == nullptr) {
-        walk_tiles<RADIX, 32>(t.status, tid, int32_t(tile) - 1, 0, excl, done, gave_up, ctrl,
-                              timeout_ns, tile, t.trace);
+        walk_tiles<RADIX, 2>(t.status, tid, int32_t(t.tile0 + tile) - 1, int32_t(t.tile0), excl,
+                             done, gave_up, ctrl, timeout_ns, tile, t.trace);
         if (!done && !gave_up) {  // tile 0 is inclusive: only if words were not cleared
           report_error(ctrl, kDevIndex, tile);
           gave_up = true;
         }
       } else {
         const int32_t g = int32_t(tile / kGroupTiles);
-        walk_tiles<RADIX, 32>(t.status, tid, int32_t(tile) - 1, g * kGroupTiles, excl, done,
-                              gave_up, ctrl, timeout_ns, tile, t.trace);
-        for (int32_t h = g - 1; !done && !gave_up && h >= 0; h -= 16) {
+        walk_tiles<RADIX, 2>(t.status, tid, int32_t(tile) - 1, g * kGroupTiles, excl, done,
+                             gave_up, ctrl, timeout_ns, tile, t.trace);
+        stamp(t.trace, 14);
+        // earlier groups, 8 per round trip (two 16-byte loads per array)
+        for (int32_t h = g - 1; !done && !gave_up && h >= 0;) {
           trace_add(t.trace, 11, 1);
-          uint32_t wi[16], wa[16];
+          const int32_t b0 = h >> 2;
+          uint4 vi[2], va[2];
 #pragma unroll
-          for (int q = 0; q < 16; ++q) {
-            wi[q] = (h - q >= 0) ? ld_relaxed(&t.ginc[size_t(h - q) * RADIX + tid]) : 0u;
-            wa[q] = (h - q >= 0) ? ld_relaxed(&t.gagg[size_t(h - q) * RADIX + tid]) : 0u;
+          for (int k = 0; k < 2; ++k) {
+            const bool in = b0 - k >= 0;
+            const size_t off = (size_t(b0 - k) * RADIX + tid) * 4;
+            vi[k] = in ? __ldcg(reinterpret_cast<const uint4*>(t.ginc + off)) : make_uint4(0, 0, 0, 0);
+            va[k] = in ? __ldcg(reinterpret_cast<const uint4*>(t.gagg + off)) : make_uint4(0, 0, 0, 0);
           }
 #pragma unroll
-          for (int q = 0; q < 16; ++q) {
-            const int32_t hh = h - q;
-            if (done || gave_up || hh < 0) continue;
-            const uint32_t fi = wi[q] & kFlagMask;
+          for (int q = 0; q < 8; ++q) {
+            const int32_t hh = 4 * b0 + 3 - q;  // groups of this window, nearest first
+            if (hh > h || hh < 0 || done || gave_up) continue;
+            const int c = 3 - (q & 3);
+            const uint4& vq = vi[q >> 2];
+            const uint4& aq = va[q >> 2];
+            const uint32_t wi = c == 0 ? vq.x : c == 1 ? vq.y : c == 2 ? vq.z : vq.w;
+            uint32_t ag = c == 0 ? aq.x : c == 1 ? aq.y : c == 2 ? aq.z : aq.w;
+            const uint32_t fi = wi & kFlagMask;
             if (fi == kFlagErr) {
               gave_up = true;
             } else if (fi == kFlagInc) {
-              excl += wi[q] & kValueMask;
+              excl += wi & kValueMask;
               done = true;
             } else {
               const uint32_t need = min(uint32_t(kGroupTiles), t.tiles - uint32_t(hh) * kGroupTiles);
-              uint32_t ag = wa[q];
               if ((ag >> 24) < need) {
                 trace_add(t.trace, 13, 1);
                 bool ok = false;
-                ag = wait_group(&t.gagg[size_t(hh) * RADIX + tid], need, ctrl, timeout_ns, tile,
-                                &ok);
+                ag = wait_group(&t.gagg[lb_index<RADIX>(uint32_t(hh), tid)], need, ctrl,
+                                timeout_ns, tile, &ok);
                 if (!ok) gave_up = true;
               }
               if (!gave_up) excl += ag & kGroupCountMask;
             }
           }
+          h = 4 * b0 - 5;  // below the lowest group of this window (4*b0 - 4)
         }
         // a walk that ran past group 0 without an inclusive prefix has summed
         // every earlier group completely
       }
       if (!t.silent)
-        st_relaxed(&t.status[size_t(tile) * RADIX + tid],
+        st_relaxed(&t.status[lb_index<RADIX>(t.tile0 + tile, tid)],
                    gave_up ? kFlagErr : (kFlagInc | ((excl + my_cnt) & kValueMask)));
     }
     if (t.ginc != nullptr && !t.silent &&
         ((tile + 1) % kGroupTiles == 0 || tile + 1 == t.tiles))
-      st_relaxed(&t.ginc[size_t(tile / kGroupTiles) * RADIX + tid],
+      st_relaxed(&t.ginc[lb_index<RADIX>(tile / kGroupTiles, tid)],
                  gave_up ? kFlagErr : (kFlagInc | ((excl + my_cnt) & kValueMask)));
     if (gave_up) s_misc[1] = 1u;
     stamp(t.trace, 9);
     s_gbase[tid] = t.pass_offsets[tid] + excl - my_start;
   }
   __syncthreads();
-  if (s_misc[1]) return false;  // the output of this call is void; ctrl->error says why
+  if (s_misc[1]) {
+    // the output of this call is void (ctrl->error says why); let the value
+    // copy land before leaving
+    if constexpr (VB > 0) {
+      bool ok = mbar_wait_bounded(&s_bar[1], 0u, ctrl, timeout_ns, tile);
+      if (!ok) mbar_wait_bounded(&s_bar[1], 0u, ctrl, timeout_ns, tile);
+      __syncthreads();
+    }
+    if (tid == 0) {
+      mbar_inval(&s_bar[0]);
+      if constexpr (VB > 0) mbar_inval(&s_bar[1]);
+    }
+    return false;
+  }
   stamp(t.trace, 4);
 
   // ---- scatter: consecutive threads take consecutive stage slots, which map
@@ -698,20 +753,31 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
     }
   }
   stamp(t.trace, 5);
+  bool ok = true;
   if constexpr (VB > 0) {
-    __syncthreads();
-    V* s_vout = reinterpret_cast<V*>(smem + S::OUT);
+    ok = mbar_wait_bounded(&s_bar[1], 0u, ctrl, timeout_ns, tile);
+    if (!ok) ok = mbar_wait_bounded(&s_bar[1], 0u, ctrl, timeout_ns, tile);
+    // every key has left the stage and the value edges are in place
+    if (!__syncthreads_or(!ok)) {
+      V* s_vout = reinterpret_cast<V*>(smem + S::OUT);
 #pragma unroll
-    for (int j = 0; j < ITEMS; ++j) s_vout[pos[j]] = s_vin[slot0 + j * 32];
-    __syncthreads();
+      for (int j = 0; j < ITEMS; ++j) s_vout[pos[j]] = s_vin[slot0 + j * 32];
+      __syncthreads();
 #pragma unroll
-    for (int s = 0; s < ITEMS; ++s) {
-      const uint32_t i = uint32_t(s * THREADS + tid);
-      if (gidx[s] != 0xffffffffu) t.vdst[gidx[s]] = s_vout[i];
+      for (int s = 0; s < ITEMS; ++s) {
+        const uint32_t i = uint32_t(s * THREADS + tid);
+        if (gidx[s] != 0xffffffffu) t.vdst[gidx[s]] = s_vout[i];
+      }
+    } else {
+      ok = false;
     }
   }
+  if (tid == 0) {
+    mbar_inval(&s_bar[0]);
+    if constexpr (VB > 0) mbar_inval(&s_bar[1]);
+  }
   stamp(t.trace, 6);
-  return true;
+  return ok;
 }
 
 // One digit pass, one tile per CTA.  The grid has one CTA per tile; tile ids
@@ -748,10 +814,12 @@ __global__ void __launch_bounds__(THREADS, MINB)
   t.mask = mask;
   t.pass_offsets = pass_offsets;
   t.status = status;
+  t.tile0 = 0u;
   t.gagg = gagg;
   t.ginc = ginc;
   t.tiles = tiles;
   t.silent = (int(t.tile) == knobs.drop_tile) && (pass == knobs.drop_pass);
+  t.lb_small = knobs.lb_small != 0;
   t.trace = (knobs.trace != nullptr && pass == knobs.trace_pass && t.tile < knobs.trace_tiles)
                 ? knobs.trace + size_t(t.tile) * 16
                 : nullptr;

@@ -77,7 +77,7 @@ struct OnesweepSort {
           static_cast<K*>(a.keys), static_cast<K*>(a.keys_alt), static_cast<V*>(a.vals),
           static_cast<V*>(a.vals_alt), a.n, p, uint32_t(lo), mask,
           reinterpret_cast<const uint32_t*>(ws + L.offsets) + size_t(p) * RADIX,
-          reinterpret_cast<uint32_t*>(ws + L.status) + size_t(p) * nt * RADIX,
+          reinterpret_cast<uint32_t*>(ws + L.status) + size_t(p) * L.tiles * RADIX,
           reinterpret_cast<uint32_t*>(ws + L.gagg) + size_t(p) * L.groups * RADIX,
           reinterpret_cast<uint32_t*>(ws + L.ginc) + size_t(p) * L.groups * RADIX, uint32_t(nt),
           ctrl, a.knobs);

@@ -57,7 +57,7 @@ inline SegLayout seg_layout(size_t n, size_t nseg, int passes, int radix_bits, i
                             int chunk) {
   SegLayout L{};
   const size_t radix = size_t(1) << radix_bits;
-  L.tiles_max = (n + tile - 1) / tile + nseg;
+  L.tiles_max = align_up((n + tile - 1) / tile + nseg, 4);
   L.chunks_max = (n + chunk - 1) / chunk + nseg;
   L.state = 256;
   L.counts = align_up(L.state + nseg * kSegStateWords * 4, 256);
@@ -286,9 +286,10 @@ __global__ void __launch_bounds__(THREADS, 2)
       const uint32_t t_first = lc * uint32_t(CHUNK_TILES);
       const uint32_t t_last = min(t_first + uint32_t(CHUNK_TILES), (d.len + TILE - 1) / TILE);
       for (int p = 0; p < passes; ++p) {
-        uint32_t* st = a.status + (size_t(p) * a.tiles_max + d.tile0 + t_first) * RADIX;
+        uint32_t* st = a.status + size_t(p) * a.tiles_max * RADIX;
         const uint32_t words = (t_last - t_first) * RADIX;
-        for (uint32_t i = tid; i < words; i += THREADS) st[i] = 0u;
+        for (uint32_t i = tid; i < words; i += THREADS)
+          st[lb_index<RADIX>(d.tile0 + t_first + i / RADIX, i % RADIX)] = 0u;
       }
       __threadfence();
       __syncthreads();
@@ -362,12 +363,14 @@ __global__ void __launch_bounds__(THREADS, 2)
         t.shift = uint32_t(lo);
         t.mask = (1u << (min(lo + RADIX_BITS, a.end_bit) - lo)) - 1u;
         t.pass_offsets = a.offsets + (size_t(li) * passes + p) * RADIX;
-        t.status = a.status + (size_t(p) * a.tiles_max + d.tile0) * RADIX;
+        t.status = a.status + size_t(p) * a.tiles_max * RADIX;
+        t.tile0 = d.tile0;
         t.gagg = nullptr;  // segments are short: flat walk
         t.ginc = nullptr;
         t.tiles = ntiles;
         t.silent = false;
         t.trace = nullptr;
+        t.lb_small = false;
         onesweep_tile<K, VB, RADIX_BITS, THREADS, ITEMS, true>(t, ctrl, a.knobs.timeout_ns,
                                                                smem);
         __threadfence();

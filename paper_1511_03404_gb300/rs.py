@@ -34,7 +34,7 @@ RS_KERNEL_KINDS = 4
 KERNEL_NAMES = ("upsweep", "onesweep", "small", "segmented")
 
 (RS_DEBUG_TIMEOUT_NS, RS_DEBUG_DROP_PUBLISH_TILE, RS_DEBUG_DROP_PUBLISH_PASS, RS_DEBUG_TRACE_PTR,
- RS_DEBUG_TRACE_TILES, RS_DEBUG_TRACE_PASS) = range(6)
+ RS_DEBUG_TRACE_TILES, RS_DEBUG_TRACE_PASS, RS_DEBUG_LB_SMALL) = range(7)
 
 
 class RsError(RuntimeError):

@@ -101,6 +101,18 @@ rs_status rs_variant_info(int key_bytes, int val_bytes, int index, int* radix_bi
                           int* threads, int* items_per_thread, int* kind, size_t* max_n);
 
 /*
+ * Tuned variant table (written by the package's autotuner): for sorts of
+ * (key_bytes, val_bytes) with no explicit configuration, n <= n_max uses
+ * `variant` (the entry with the smallest n_max >= n wins; n above every
+ * entry falls back to the built-in choice).  Setting an existing n_max
+ * replaces its variant.  RS_ERR_INVALID for an unknown type or variant.
+ * Workspace sizes follow the table: query rs_workspace_bytes after changing
+ * it.  rs_tune_clear drops every entry.
+ */
+rs_status rs_tune_set(int key_bytes, int val_bytes, size_t n_max, int variant);
+rs_status rs_tune_clear(void);
+
+/*
  * Workspace bytes a sort of n elements over [begin_bit, end_bit) needs with
  * configuration cfg (NULL = library choice).  The sort entry points with the
  * same arguments accept any workspace at least this large.

@@ -1,6 +1,7 @@
 // C ABI of the rs library (declared in include/rs.h): argument checks,
 // variant choice, workspace sizing, device-status readback, per-kernel
 // event timing and the test-only fault-injection knobs.
+#include <algorithm>
 #include <atomic>
 #include <cstring>
 #include <map>
@@ -143,6 +144,27 @@ void prof_after(cudaStream_t s, int kind, double bytes, int slot, int pass) {
   p.recs.push_back(ProfRec{kind, bytes, slot, pass});
 }
 
+// ------------------------------------------------------------ tuned table
+
+namespace {
+struct TuneEntry {
+  size_t n_max;
+  int variant;
+};
+std::mutex g_tune_mu;
+std::map<int, std::vector<TuneEntry>> g_tune;  // key: key_bytes * 16 + val_bytes
+}  // namespace
+
+// The tuned variant for n elements of (kb, vb), or -1.
+static int tuned_variant(int kb, int vb, size_t n) {
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  auto it = g_tune.find(kb * 16 + vb);
+  if (it == g_tune.end()) return -1;
+  for (const TuneEntry& e : it->second)
+    if (n <= e.n_max) return e.variant;
+  return -1;
+}
+
 // -------------------------------------------------------------- choosing
 
 static const Variant* choose(int kb, int vb, size_t n, const rs_config* cfg) {
@@ -155,6 +177,10 @@ static const Variant* choose(int kb, int vb, size_t n, const rs_config* cfg) {
     const Variant* c = &v[cfg->variant];
     if (want_r && c->radix_bits != want_r) return nullptr;
     return n <= c->max_n ? c : nullptr;
+  }
+  if (!want_r) {
+    const int tv = tuned_variant(kb, vb, n);
+    if (tv >= 0 && tv < count && n <= v[tv].max_n) return &v[tv];
   }
   // default: one CTA when the array fits a small-sort tile, else onesweep
   const Variant* best = nullptr;
@@ -396,6 +422,30 @@ rs_status rs_profile_end(int* launches, double* ms, double* bytes) {
   }
   p.release();
   return st;
+}
+
+rs_status rs_tune_set(int key_bytes, int val_bytes, size_t n_max, int variant) {
+  int count = 0;
+  const Variant* v = variants(key_bytes, val_bytes, &count);
+  if (!v || variant < 0 || variant >= count) return RS_ERR_INVALID;
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  auto& list = g_tune[key_bytes * 16 + val_bytes];
+  bool replaced = false;
+  for (TuneEntry& e : list)
+    if (e.n_max == n_max) {
+      e.variant = variant;
+      replaced = true;
+    }
+  if (!replaced) list.push_back(TuneEntry{n_max, variant});
+  std::sort(list.begin(), list.end(),
+            [](const TuneEntry& a, const TuneEntry& b) { return a.n_max < b.n_max; });
+  return RS_OK;
+}
+
+rs_status rs_tune_clear(void) {
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  g_tune.clear();
+  return RS_OK;
 }
 
 rs_status rs_debug_set(rs_debug_knob knob, long long value) {

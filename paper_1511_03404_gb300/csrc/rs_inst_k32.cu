@@ -1,4 +1,6 @@
-// Compiled variants of the sort for keys only, uint32_t keys.
+// Compiled variants of the sort for 32-bit keys (keys only).  Index 0 is the
+// default multi-CTA shape; the others are candidates for the autotuner
+// (tile shape, registers per thread, digit width).
 #include "rs_launch.cuh"
 
 namespace rs {
@@ -7,6 +9,10 @@ const Variant* variants_k32(int* count) {
   static const Variant table[] = {
       OnesweepSort<uint32_t, 0, 8, 256, 16, 4>::describe(),
       SmallSort<uint32_t, 0, 8, 512, 16>::describe(),
+      OnesweepSort<uint32_t, 0, 8, 256, 12, 4>::describe(),
+      OnesweepSort<uint32_t, 0, 8, 256, 20, 3>::describe(),
+      OnesweepSort<uint32_t, 0, 7, 256, 16, 4>::describe(),
+      SmallSort<uint32_t, 0, 8, 256, 16>::describe(),
   };
   *count = int(sizeof(table) / sizeof(table[0]));
   return table;

@@ -92,6 +92,8 @@ _SIGS = {
     "rs_cancel": ([_vp, ctypes.c_uint64], _i),
     "rs_server_stats": ([_vp, _vp], _i),
     "rs_server_reset_stats": ([_vp], _i),
+    "rs_tune_set": ([_i, _i, _sz, _i], _i),
+    "rs_tune_clear": ([], _i),
     "rs_profile_begin": ([_i], _i),
     "rs_profile_end": ([_vp, _vp, _vp], _i),
     "rs_debug_set": ([_i, ctypes.c_longlong], _i),
@@ -116,7 +118,29 @@ def load():
                 fn.argtypes = args
                 fn.restype = res
             _lib = lib
+            _apply_tuned_table(lib)
     return _lib
+
+
+TUNED_TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned.json")
+
+
+def _apply_tuned_table(lib, path: str | None = None) -> int:
+    """Load the autotuner's table (tuned.json next to this file) into the library.
+
+    Returns the number of entries applied (0 when there is no table, or when
+    RS_NO_TUNED_TABLE is set)."""
+    import json
+    path = path or TUNED_TABLE
+    if os.environ.get("RS_NO_TUNED_TABLE") or not os.path.exists(path):
+        return 0
+    with open(path) as f:
+        table = json.load(f)
+    applied = 0
+    for e in table.get("entries", []):
+        if lib.rs_tune_set(e["key_bytes"], e["val_bytes"], e["n_max"], e["variant"]) == RS_OK:
+            applied += 1
+    return applied
 
 
 def declared_symbols() -> list[str]:
@@ -278,6 +302,14 @@ def rs_server_stats(server):
 
 def rs_server_reset_stats(server) -> int:
     return load().rs_server_reset_stats(server)
+
+
+def rs_tune_set(key_bytes: int, val_bytes: int, n_max: int, variant: int) -> int:
+    return load().rs_tune_set(key_bytes, val_bytes, n_max, variant)
+
+
+def rs_tune_clear() -> int:
+    return load().rs_tune_clear()
 
 
 def rs_profile_begin(capacity: int) -> int:

@@ -44,18 +44,20 @@ WORKLOAD = ("u32 key + u32 value (value = index) pairs, n=2^26, mt19937 seed 1, 
 L2_FLUSH_BYTES = 256 << 20
 
 # DRAM traffic of one onesweep launch from an ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum), keyed by the hash of the kernel sources it was taken
-# on; when the sources change the figure no longer applies and traffic is null.
+# dram__bytes_write.sum of pass 0 of a 2^26-pair sort), keyed by the hash of the
+# kernel sources it was taken on; when they change the figure no longer applies
+# and traffic is null.
 NCU_TRAFFIC = {}
+
+ONESWEEP_SOURCES = ("rs_kernels.cuh", "rs_common.h", "rs_launch.cuh", "rs_inst_kv32.cu")
 
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1511_03404_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cuh", ".cu", ".h")):
-            with open(os.path.join(csrc, f), "rb") as fh:
-                h.update(fh.read())
+    for f in ONESWEEP_SOURCES:
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
@@ -303,8 +305,8 @@ def run_ours(args):
     traffic = None
     src = kernel_source_hash()
     t = NCU_TRAFFIC.get(src)
-    if t is not None:
-        traffic = t
+    if t is not None and t.get("n") == n:
+        traffic = t["bytes_per_launch"]
     line = {
         "metric": METRIC, "value": value, "unit": "Gkeys/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -332,6 +334,10 @@ def run_ours(args):
         "kernel_source": src,
     }
     if not (args.no_extras or args.quick) and world == 1:
+        stage("u32 keys, 2^20 (launch-bound)")
+        line["u32_keys_2p20"] = bench_u32_keys_small(torch, rs, dev)
+        stage("u64 keys and pairs, 2^27")
+        line["u64_2p27"] = bench_u64(torch, rs, dev)
         stage("segmented: batched vs plain")
         line["segmented"] = bench_segmented(torch, rs, dev, args.seg_scaled)
         stage("serving: Poisson trace")
@@ -406,6 +412,100 @@ def e2e_rate(torch, rs, keys_h, vals_h, n, dev, ws, args, dists) -> dict:
     torch.cuda.synchronize()
     ms = t0.elapsed_time(t1) / steps
     return {"value": n / (ms / 1e3) / 1e9, "ms_per_step": ms, "h2d": 2 * 4 * n, "d2h": 2 * 4 * n}
+
+
+def _time_sorts(torch, rs, kb, vb, keys, vals, reps, stream):
+    """Median CUDA-event time (ms) of `reps` sorts of fresh copies of keys/vals."""
+    n = keys.numel()
+    k, ka = torch.empty_like(keys), torch.empty_like(keys)
+    v = torch.empty_like(vals) if vb else None
+    va = torch.empty_like(vals) if vb else None
+    st, need = rs.rs_workspace_bytes(kb, vb, n, 0, 8 * kb)
+    rs.check(st, "rs_workspace_bytes")
+    ws = torch.empty(max(need, 256), dtype=torch.uint8, device=keys.device)
+    h = stream.cuda_stream
+    times = []
+    for r in range(reps + 2):
+        k.copy_(keys)
+        if vb:
+            v.copy_(vals)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st, _ = rs.rs_sort(kb, vb, k.data_ptr(), v.data_ptr() if vb else None, ka.data_ptr(),
+                           va.data_ptr() if vb else None, n, 0, 8 * kb, ws.data_ptr(),
+                           ws.numel(), h)
+        e1.record(stream)
+        rs.check(st, "rs_sort")
+        stream.synchronize()
+        if r >= 2:
+            times.append(e0.elapsed_time(e1))
+    rs.check(rs.rs_workspace_status(ws.data_ptr(), h)[0], "device status")
+    return statistics.median(times)
+
+
+def bench_u32_keys_small(torch, rs, dev, reps: int = 20) -> dict:
+    """32-bit keys only, n = 2^20, uniform: a launch-bound, L2-resident sort,
+    timed per call and as a replayed CUDA graph of the same call."""
+    n = 1 << 20
+    keys = torch.from_numpy(inputs.keys(np.uint32, "uniform", n).view(np.int32)).to(dev)
+    stream = torch.cuda.Stream(dev)
+    with torch.cuda.stream(stream):
+        ms = _time_sorts(torch, rs, 4, 0, keys, None, reps, stream)
+    k, ka = torch.empty_like(keys), torch.empty_like(keys)
+    st, need = rs.rs_workspace_bytes(4, 0, n, 0, 32)
+    ws = torch.empty(max(need, 256), dtype=torch.uint8, device=dev)
+    h = stream.cuda_stream
+    with torch.cuda.stream(stream):
+        k.copy_(keys)
+        rs.check(rs.rs_sort_keys_u32(k.data_ptr(), ka.data_ptr(), n, 0, 32, ws.data_ptr(),
+                                     ws.numel(), h)[0])
+    stream.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        st, in_alt = rs.rs_sort_keys_u32(k.data_ptr(), ka.data_ptr(), n, 0, 32, ws.data_ptr(),
+                                         ws.numel(), h)
+    rs.check(st, "captured sort")
+    times = []
+    for r in range(reps + 2):
+        with torch.cuda.stream(stream):
+            k.copy_(keys)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            graph.replay()
+            e1.record(stream)
+        stream.synchronize()
+        if r >= 2:
+            times.append(e0.elapsed_time(e1))
+    gms = statistics.median(times)
+    out_k = (ka if in_alt else k).cpu().numpy().view(np.uint32)
+    if not np.array_equal(out_k, np.sort(keys.cpu().numpy().view(np.uint32))):
+        raise SystemExit("bench: 2^20-key sort (graph replay) is not sorted")
+    return {"workload": "u32 keys only, n=2^20, uniform, 8-bit digits (4 passes); inputs fit L2",
+            "ms": ms, "gkeys_per_s": n / (ms / 1e3) / 1e9,
+            "graph_ms": gms, "graph_gkeys_per_s": n / (gms / 1e3) / 1e9}
+
+
+def bench_u64(torch, rs, dev, reps: int = 3) -> dict:
+    """64-bit keys and 64-bit pairs, n = 2^27: uniform, gaussian and 16-bit
+    entropy keys (the last skips six of eight digit passes)."""
+    n = 1 << 27
+    stream = torch.cuda.Stream(dev)
+    out = {}
+    vals = torch.from_numpy(np.arange(n, dtype=np.int64)).to(dev)
+    for dist in ("uniform", "gaussian", "entropy16"):
+        keys = torch.from_numpy(inputs.keys(np.uint64, dist, n).view(np.int64)).to(dev)
+        with torch.cuda.stream(stream):
+            mk = _time_sorts(torch, rs, 8, 0, keys, None, reps, stream)
+            mkv = _time_sorts(torch, rs, 8, 8, keys, vals, reps, stream)
+        out[dist] = {"keys_ms": mk, "keys_gkeys_per_s": n / (mk / 1e3) / 1e9,
+                     "pairs_ms": mkv, "pairs_gkeys_per_s": n / (mkv / 1e3) / 1e9}
+        del keys
+    del vals
+    torch.cuda.empty_cache()
+    out["workload"] = "n=2^27, 64-bit keys / 64-bit key + 64-bit value pairs, 8-bit digits"
+    return out
 
 
 def bench_segmented(torch, rs, dev, scaled: bool, reps: int = 3) -> dict:

@@ -94,8 +94,9 @@ int rs_num_variants(int key_bytes, int val_bytes);
 
 /*
  * Describe variant `index` of (key_bytes, val_bytes): digit width, threads
- * per CTA, keys per thread, and kind (0 = multi-CTA onesweep, 1 = one CTA
- * sorting the whole array in shared memory; max_n bounds the latter).
+ * per CTA, keys per thread, and kind (0 = multi-CTA onesweep with one CTA per
+ * tile, 1 = one CTA sorting the whole array in shared memory, 2 = onesweep on
+ * resident CTAs that each take tile after tile); max_n bounds the array size.
  */
 rs_status rs_variant_info(int key_bytes, int val_bytes, int index, int* radix_bits,
                           int* threads, int* items_per_thread, int* kind, size_t* max_n);

@@ -58,7 +58,7 @@ def _time_variant(torch, kb, vb, n, variant, keys, vals, reps):
     return statistics.median(times)
 
 
-def tune(sizes=SIZES, types=TYPES, reps=5, log=print) -> dict:
+def tune(sizes=SIZES, types=TYPES, reps=5, log=print, verbose=False) -> dict:
     import torch
 
     rs.load()
@@ -79,6 +79,8 @@ def tune(sizes=SIZES, types=TYPES, reps=5, log=print) -> dict:
             for i, info in enumerate(infos):
                 if n > info["max_n"]:
                     continue
+                if verbose:
+                    print(f"  k{kb} v{vb} n={n} variant {i}", file=sys.stderr, flush=True)
                 ms = _time_variant(torch, kb, vb, n, i, keys, vals, reps)
                 if ms is not None:
                     results[i] = ms
@@ -101,9 +103,10 @@ def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--out", default=rs.TUNED_TABLE)
     ap.add_argument("--quick", action="store_true", help="fewer sizes and repetitions")
+    ap.add_argument("--verbose", action="store_true", help="name each variant before timing it")
     args = ap.parse_args(argv)
     sizes = (2**12, 2**16, 2**20, 2**24) if args.quick else SIZES
-    table = tune(sizes=sizes, reps=3 if args.quick else 5)
+    table = tune(sizes=sizes, reps=3 if args.quick else 5, verbose=args.verbose)
     with open(args.out, "w") as f:
         json.dump(table, f, indent=1)
         f.write("\n")

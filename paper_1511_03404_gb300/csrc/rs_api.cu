@@ -189,7 +189,7 @@ static const Variant* choose(int kb, int vb, size_t n, const rs_config* cfg) {
     if (want_r && c->radix_bits != want_r) continue;
     if (n > c->max_n) continue;
     if (c->kind == kSmall && (!best || best->kind != kSmall)) best = c;
-    if (c->kind == kOnesweep && !best) best = c;
+    if ((c->kind == kOnesweep || c->kind == kOnesweepPersist) && !best) best = c;
   }
   return best;
 }
@@ -332,7 +332,7 @@ rs_status rs_digit_counts(int key_bytes, const void* keys, size_t n, int begin_b
   const Variant* all = variants(key_bytes, 0, &count);
   const Variant* v = nullptr;
   for (int i = 0; i < count && !v; ++i)
-    if (all[i].kind == kOnesweep && all[i].radix_bits == radix_bits) v = &all[i];
+    if (all[i].kind != kSmall && all[i].radix_bits == radix_bits) v = &all[i];
   if (!v) return RS_ERR_INVALID;
   const int passes = num_passes(begin_bit, end_bit, radix_bits);
   const Layout L = onesweep_layout(passes, radix_bits, 0);

@@ -25,7 +25,7 @@ struct SortArgs {
   Knobs knobs;
 };
 
-enum VariantKind { kOnesweep = 0, kSmall = 1 };
+enum VariantKind { kOnesweep = 0, kSmall = 1, kOnesweepPersist = 2 };
 
 struct Variant {
   int key_bytes, val_bytes;

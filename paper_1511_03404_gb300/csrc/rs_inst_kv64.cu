@@ -11,6 +11,7 @@ const Variant* variants_kv64(int* count) {
       OnesweepSort<uint64_t, 8, 8, 256, 8, 3>::describe(),
       OnesweepSort<uint64_t, 8, 8, 256, 16, 2>::describe(),
       SmallSort<uint64_t, 8, 8, 256, 16>::describe(),
+      OnesweepSort<uint64_t, 8, 8, 256, 12, 2, true>::describe(),
   };
   *count = int(sizeof(table) / sizeof(table[0]));
   return table;

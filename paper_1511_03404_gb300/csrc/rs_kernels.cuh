@@ -292,8 +292,8 @@ struct OnesweepSmem {
   static constexpr int TSTART = CNT + RADIX * 4;           // u32 [RADIX] tile digit starts
   static constexpr int GBASE = TSTART + RADIX * 4;         // u32 [RADIX] global base
   static constexpr int TOT = GBASE + RADIX * 4;            // u32 [32]
-  static constexpr int MISC = TOT + 32 * 4;                // u32 [4]: tile, abort, ...
-  static constexpr int MBAR = MISC + 16;                   // u64 [2] mbarriers: keys, values
+  static constexpr int MISC = TOT + 32 * 4;                // u32 [8]: tile, abort, next tile, ...
+  static constexpr int MBAR = MISC + 32;                   // u64 [2] mbarriers: keys, values
   // the tile's keys as loaded (+16 B skew); once they are staged in OUT, the
   // tile's values are loaded here
   static constexpr int KIN = (MBAR + 16 + 15) / 16 * 16;
@@ -506,15 +506,57 @@ struct Stage {
   }
 };
 
+// Start staging the keys of tile `tile` of an array of n keys into the key
+// buffer: one bulk copy issued by thread 0 on `bar`, head/tail elements and
+// the past-the-end sentinels written by every thread.
+template <class K, int THREADS, int TILE, bool CG>
+__device__ __forceinline__ void stage_keys(unsigned char* kin, const K* ksrc, uint32_t n,
+                                           uint32_t tile, uint64_t* bar) {
+  const uint32_t tile_base = tile * uint32_t(TILE);
+  const uint32_t tile_len = min(uint32_t(TILE), n - tile_base);
+  const K* gk = ksrc + tile_base;
+  const Stage<K> sk(gk, tile_len);
+  if (threadIdx.x == 0) {
+    // shared memory this CTA used through ordinary loads and stores before is
+    // about to be written by the copy engine; and, when the source was written
+    // by other CTAs of this kernel, those stores must be ordered before the
+    // copy engine reads them
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if constexpr (CG) asm volatile("fence.proxy.async.global;" ::: "memory");
+    mbar_arrive_expect_tx(bar, sk.body);
+    sk.issue(kin, gk, bar);
+  }
+  sk.edges(kin, gk, tile_len);
+  // past the end: the largest digit, so these items rank after every key of
+  // the tile and are never written out
+  K* s_kin = sk.at(kin);
+  for (uint32_t i = tile_len + threadIdx.x; i < uint32_t(TILE); i += THREADS) s_kin[i] = ~K(0);
+}
+
+// Persistent CTAs: where the next tile id comes from.
+struct Prefetch {
+  uint32_t* counter;  // the pass's tile counter
+  uint32_t tiles;
+};
+
 // One tile of one counting-sort pass (Sec. 2.6): stage the tile's keys in
 // shared memory, rank them, publish the tile's digit counts, look back, and
 // scatter stably; the values are fetched into the freed key buffer while the
 // look-back and the key scatter run.  Every thread of the CTA calls it.
 // Returns false (CTA-uniform) when a bounded wait gave up, in which case
 // nothing of this tile was written and no copy into shared memory is pending.
-template <class K, int VB, int RADIX_BITS, int THREADS, int ITEMS, bool CG>
+//
+// PERSIST: the calling kernel keeps the CTA resident over many tiles.  The
+// barriers are initialised once by the kernel, this tile's keys were staged
+// by the previous call (or the kernel's prologue) on barrier phase `parity`,
+// and as soon as the key buffer is free again this call takes the next tile
+// id (s_misc[3]) and starts staging its keys (s_misc[4] = 1), overlapping the
+// end of this tile.
+template <class K, int VB, int RADIX_BITS, int THREADS, int ITEMS, bool CG, bool PERSIST = false>
 __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ctrl,
-                                              uint64_t timeout_ns, unsigned char* smem) {
+                                              uint64_t timeout_ns, unsigned char* smem,
+                                              uint32_t parity = 0u,
+                                              const Prefetch* pf = nullptr) {
   using V = ValT<VB>;
   using S = OnesweepSmem<K, VB, RADIX_BITS, THREADS, ITEMS>;
   constexpr int RADIX = S::RADIX, WARPS = S::WARPS, TILE = S::TILE;
@@ -536,41 +578,29 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
   stamp(t.trace, 0);
   if (t.trace != nullptr && tid == 0) t.trace[7] = sm_id();
 
-  if (tid == 0) {
-    mbar_init(&s_bar[0]);
-    if constexpr (VB > 0) mbar_init(&s_bar[1]);
-    s_misc[1] = 0u;
+  if constexpr (!PERSIST) {
+    if (tid == 0) {
+      mbar_init(&s_bar[0]);
+      if constexpr (VB > 0) mbar_init(&s_bar[1]);
+    }
+    __syncthreads();
+    // ---- stage the tile's keys
+    stage_keys<K, THREADS, TILE, CG>(smem + S::KIN, t.ksrc, n, tile, &s_bar[0]);
   }
-  __syncthreads();
-
-  // ---- stage the tile's keys
-  const K* gk = t.ksrc + tile_base;
-  const Stage<K> sk(gk, tile_len);
-  K* s_kin = sk.at(smem + S::KIN);
-  if (tid == 0) {
-    // shared memory this CTA used through ordinary loads and stores before
-    // (an earlier work item) is about to be written by the copy engine; and,
-    // when the source was written by other CTAs of this kernel, those stores
-    // must be ordered before the copy engine reads them
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    if constexpr (CG) asm volatile("fence.proxy.async.global;" ::: "memory");
-    mbar_arrive_expect_tx(&s_bar[0], sk.body);
-    sk.issue(smem + S::KIN, gk, &s_bar[0]);
-  }
-  sk.edges(smem + S::KIN, gk, tile_len);
-  // past the end: the largest digit, so these items rank after every key of
-  // the tile and are never written out
-  for (uint32_t i = tile_len + tid; i < uint32_t(TILE); i += THREADS) s_kin[i] = ~K(0);
+  if (tid == 0) s_misc[1] = 0u;
+  K* s_kin = Stage<K>(t.ksrc + tile_base, tile_len).at(smem + S::KIN);
   for (int i = tid; i < WARPS * RADIX; i += THREADS) {
     s_wh[i] = 0u;
     s_mm[i] = 0u;
   }
-  bool landed = mbar_wait_bounded(&s_bar[0], 0u, ctrl, timeout_ns, tile);
-  if (!landed) landed = mbar_wait_bounded(&s_bar[0], 0u, ctrl, timeout_ns, tile);
+  bool landed = mbar_wait_bounded(&s_bar[0], parity, ctrl, timeout_ns, tile);
+  if (!landed) landed = mbar_wait_bounded(&s_bar[0], parity, ctrl, timeout_ns, tile);
   if (__syncthreads_or(!landed)) {  // CTA-uniform
-    if (tid == 0) {
-      mbar_inval(&s_bar[0]);
-      if constexpr (VB > 0) mbar_inval(&s_bar[1]);
+    if constexpr (!PERSIST) {
+      if (tid == 0) {
+        mbar_inval(&s_bar[0]);
+        if constexpr (VB > 0) mbar_inval(&s_bar[1]);
+      }
     }
     return false;
   }
@@ -722,17 +752,29 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
     // the output of this call is void (ctrl->error says why); let the value
     // copy land before leaving
     if constexpr (VB > 0) {
-      bool ok = mbar_wait_bounded(&s_bar[1], 0u, ctrl, timeout_ns, tile);
-      if (!ok) mbar_wait_bounded(&s_bar[1], 0u, ctrl, timeout_ns, tile);
+      bool ok = mbar_wait_bounded(&s_bar[1], parity, ctrl, timeout_ns, tile);
+      if (!ok) mbar_wait_bounded(&s_bar[1], parity, ctrl, timeout_ns, tile);
       __syncthreads();
     }
-    if (tid == 0) {
-      mbar_inval(&s_bar[0]);
-      if constexpr (VB > 0) mbar_inval(&s_bar[1]);
+    if constexpr (!PERSIST) {
+      if (tid == 0) {
+        mbar_inval(&s_bar[0]);
+        if constexpr (VB > 0) mbar_inval(&s_bar[1]);
+      }
     }
     return false;
   }
   stamp(t.trace, 4);
+  // keys only: the key buffer is free (keys are staged in OUT) -- start the next tile
+  if constexpr (PERSIST && VB == 0) {
+    if (tid == 0) {
+      const uint32_t nxt = atomicAdd(pf->counter, 1u);
+      s_misc[3] = nxt;
+      s_misc[4] = nxt < pf->tiles ? 1u : 0u;
+    }
+    __syncthreads();
+    if (s_misc[4]) stage_keys<K, THREADS, TILE, CG>(smem + S::KIN, t.ksrc, n, s_misc[3], &s_bar[0]);
+  }
 
   // ---- scatter: consecutive threads take consecutive stage slots, which map
   // to consecutive output addresses inside each digit run
@@ -755,14 +797,26 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
   stamp(t.trace, 5);
   bool ok = true;
   if constexpr (VB > 0) {
-    ok = mbar_wait_bounded(&s_bar[1], 0u, ctrl, timeout_ns, tile);
-    if (!ok) ok = mbar_wait_bounded(&s_bar[1], 0u, ctrl, timeout_ns, tile);
+    ok = mbar_wait_bounded(&s_bar[1], parity, ctrl, timeout_ns, tile);
+    if (!ok) ok = mbar_wait_bounded(&s_bar[1], parity, ctrl, timeout_ns, tile);
     // every key has left the stage and the value edges are in place
     if (!__syncthreads_or(!ok)) {
       V* s_vout = reinterpret_cast<V*>(smem + S::OUT);
 #pragma unroll
       for (int j = 0; j < ITEMS; ++j) s_vout[pos[j]] = s_vin[slot0 + j * 32];
+      if constexpr (PERSIST) {
+        // the key buffer is free (values are staged in OUT): start the next tile
+        if (tid == 0) {
+          const uint32_t nxt = atomicAdd(pf->counter, 1u);
+          s_misc[3] = nxt;
+          s_misc[4] = nxt < pf->tiles ? 1u : 0u;
+        }
+      }
       __syncthreads();
+      if constexpr (PERSIST) {
+        if (s_misc[4])
+          stage_keys<K, THREADS, TILE, CG>(smem + S::KIN, t.ksrc, n, s_misc[3], &s_bar[0]);
+      }
 #pragma unroll
       for (int s = 0; s < ITEMS; ++s) {
         const uint32_t i = uint32_t(s * THREADS + tid);
@@ -772,9 +826,11 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
       ok = false;
     }
   }
-  if (tid == 0) {
-    mbar_inval(&s_bar[0]);
-    if constexpr (VB > 0) mbar_inval(&s_bar[1]);
+  if constexpr (!PERSIST) {
+    if (tid == 0) {
+      mbar_inval(&s_bar[0]);
+      if constexpr (VB > 0) mbar_inval(&s_bar[1]);
+    }
   }
   stamp(t.trace, 6);
   return ok;
@@ -824,6 +880,88 @@ __global__ void __launch_bounds__(THREADS, MINB)
                 ? knobs.trace + size_t(t.tile) * 16
                 : nullptr;
   onesweep_tile<K, VB, RADIX_BITS, THREADS, ITEMS, false>(t, ctrl, knobs.timeout_ns, smem);
+}
+
+// One digit pass with resident CTAs (a grid of SMs x resident CTAs): each CTA
+// takes tiles from the pass's atomic counter one after another and starts
+// loading its next tile while it finishes the current one.  Tile ids are
+// still taken in order by running CTAs, so the look-back keeps making
+// progress: the lowest unfinished tile is always being worked on.
+template <class K, int VB, int RADIX_BITS, int THREADS, int ITEMS, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB)
+    k_onesweep_persist(K* __restrict__ k0, K* __restrict__ k1, ValT<VB>* __restrict__ v0,
+                       ValT<VB>* __restrict__ v1, uint32_t n, int pass, uint32_t shift,
+                       uint32_t mask, const uint32_t* __restrict__ pass_offsets,
+                       uint32_t* __restrict__ status, uint32_t* __restrict__ gagg,
+                       uint32_t* __restrict__ ginc, uint32_t tiles, Ctrl* __restrict__ ctrl,
+                       Knobs knobs) {
+  using S = OnesweepSmem<K, VB, RADIX_BITS, THREADS, ITEMS>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint32_t* s_misc = reinterpret_cast<uint32_t*>(smem + S::MISC);
+  uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem + S::MBAR);
+
+  const uint32_t exec = ctrl->exec_mask;
+  if (!((exec >> pass) & 1u)) return;  // every key has the same digit: nothing moves
+  const bool from_alt = (__popc(exec & ((1u << pass) - 1u)) & 1) != 0;
+  Prefetch pf{&ctrl->tile_counter[pass], tiles};
+  if (threadIdx.x == 0) {
+    mbar_init(&s_bar[0]);
+    if constexpr (VB > 0) mbar_init(&s_bar[1]);
+    s_misc[3] = atomicAdd(pf.counter, 1u);
+    s_misc[2] = ld_relaxed(&ctrl->error);  // an earlier pass of this call gave up
+  }
+  __syncthreads();
+  TileArgs<K, VB> t;
+  t.ksrc = from_alt ? k1 : k0;
+  t.kdst = from_alt ? k0 : k1;
+  t.vsrc = from_alt ? v1 : v0;
+  t.vdst = from_alt ? v0 : v1;
+  t.n = n;
+  t.shift = shift;
+  t.mask = mask;
+  t.pass_offsets = pass_offsets;
+  t.status = status;
+  t.tile0 = 0u;
+  t.gagg = gagg;
+  t.ginc = ginc;
+  t.tiles = tiles;
+  t.lb_small = knobs.lb_small != 0;
+  uint32_t tile = s_misc[3];
+  if (tile < tiles && s_misc[2] == 0u)
+    stage_keys<K, THREADS, S::TILE, false>(smem + S::KIN, t.ksrc, n, tile, &s_bar[0]);
+  else
+    tile = tiles;  // nothing to do
+  if (threadIdx.x == 0) s_misc[4] = 0u;
+  __syncthreads();
+  for (uint32_t it = 0; tile < tiles; ++it) {
+    t.tile = tile;
+    t.silent = (int(tile) == knobs.drop_tile) && (pass == knobs.drop_pass);
+    t.trace = (knobs.trace != nullptr && pass == knobs.trace_pass && tile < knobs.trace_tiles)
+                  ? knobs.trace + size_t(tile) * 16
+                  : nullptr;
+    const bool ok = onesweep_tile<K, VB, RADIX_BITS, THREADS, ITEMS, false, true>(
+        t, ctrl, knobs.timeout_ns, smem, it & 1u, &pf);
+    __syncthreads();
+    const bool next = s_misc[4] != 0u;
+    const uint32_t next_tile = s_misc[3];
+    __syncthreads();  // every thread has read the next tile before it is cleared
+    if (threadIdx.x == 0) s_misc[4] = 0u;
+    if (!ok) {
+      // a bounded wait gave up: let the next tile's key copy land, then stop
+      if (next) {
+        bool done = mbar_wait_bounded(&s_bar[0], (it + 1u) & 1u, ctrl, knobs.timeout_ns, tile);
+        if (!done) mbar_wait_bounded(&s_bar[0], (it + 1u) & 1u, ctrl, knobs.timeout_ns, tile);
+        __syncthreads();
+      }
+      break;
+    }
+    tile = next ? next_tile : tiles;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_inval(&s_bar[0]);
+    if constexpr (VB > 0) mbar_inval(&s_bar[1]);
+  }
 }
 
 // ------------------------------------------------------------ small sort

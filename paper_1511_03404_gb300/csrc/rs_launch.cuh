@@ -11,7 +11,9 @@
 
 namespace rs {
 
-template <class K, int VB, int R, int THREADS, int ITEMS, int MINB>
+// PERSIST: the passes run as k_onesweep_persist on a grid of SMs x resident
+// CTAs instead of one CTA per tile.
+template <class K, int VB, int R, int THREADS, int ITEMS, int MINB, bool PERSIST = false>
 struct OnesweepSort {
   static constexpr int RADIX = 1 << R;
   static constexpr int TILE = THREADS * ITEMS;
@@ -64,16 +66,21 @@ struct OnesweepSort {
     Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws);
     const int slot = prof_note_mask(a.stream, &ctrl->exec_mask);
     using V = ValT<VB>;
-    auto kern = &k_onesweep<K, VB, R, THREADS, ITEMS, MINB>;
-    if (prepare_kernel(reinterpret_cast<const void*>(kern), THREADS, S::BYTES) <= 0)
-      return cudaErrorInvalidConfiguration;
+    auto kern = [] {  // instantiate only the kernel this variant launches
+      if constexpr (PERSIST) return &k_onesweep_persist<K, VB, R, THREADS, ITEMS, MINB>;
+      else return &k_onesweep<K, VB, R, THREADS, ITEMS, MINB>;
+    }();
+    const int occ = prepare_kernel(reinterpret_cast<const void*>(kern), THREADS, S::BYTES);
+    if (occ <= 0) return cudaErrorInvalidConfiguration;
+    const unsigned grid =
+        PERSIST ? unsigned(std::min<size_t>(nt, size_t(device_info().sms) * occ)) : unsigned(nt);
     const double bytes = 2.0 * double(a.n) * double(sizeof(K) + VB);
     for (int p = 0; p < passes; ++p) {
       const int lo = a.begin_bit + p * R;
       const int width = std::min(R, a.end_bit - lo);
       const uint32_t mask = (1u << width) - 1u;
       prof_before(a.stream);
-      kern<<<unsigned(nt), THREADS, S::BYTES, a.stream>>>(
+      kern<<<grid, THREADS, S::BYTES, a.stream>>>(
           static_cast<K*>(a.keys), static_cast<K*>(a.keys_alt), static_cast<V*>(a.vals),
           static_cast<V*>(a.vals_alt), a.n, p, uint32_t(lo), mask,
           reinterpret_cast<const uint32_t*>(ws + L.offsets) + size_t(p) * RADIX,
@@ -98,7 +105,7 @@ struct OnesweepSort {
     Variant v{};
     v.key_bytes = int(sizeof(K));
     v.val_bytes = VB;
-    v.kind = kOnesweep;
+    v.kind = PERSIST ? kOnesweepPersist : kOnesweep;
     v.radix_bits = R;
     v.threads = THREADS;
     v.items = ITEMS;

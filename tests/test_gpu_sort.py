@@ -61,6 +61,21 @@ def test_every_variant_tile_boundaries(dtype, pairs):
 
 
 @pytest.mark.parametrize("dtype,pairs", TYPES, ids=TYPE_IDS)
+def test_resident_cta_variants_many_tiles_per_cta(dtype, pairs):
+    """Variants whose CTAs stay resident and take tile after tile: sizes that
+    give every CTA several tiles (the boundary test above gives each one)."""
+    kb = np.dtype(dtype).itemsize
+    vb = kb if pairs else 0
+    for var in variants(kb, vb):
+        if var["kind"] != 2:
+            continue
+        tile = var["threads"] * var["items"]
+        for n in (152 * 4 * tile * 3 + 12345, 152 * 4 * tile * 5):
+            check_case(dtype, pairs, "uniform", n, variant=var["index"])
+        check_case(dtype, pairs, "sorted_desc", 152 * 4 * tile * 2 + 7, variant=var["index"])
+
+
+@pytest.mark.parametrize("dtype,pairs", TYPES, ids=TYPE_IDS)
 def test_typed_entry_points(dtype, pairs):
     for n in (5000, 70001):
         check_case(dtype, pairs, "bucket", n, api="typed")

@@ -14,6 +14,7 @@ const Variant* variants_k32(int* count) {
       OnesweepSort<uint32_t, 0, 7, 256, 16, 4>::describe(),
       SmallSort<uint32_t, 0, 8, 256, 16>::describe(),
       OnesweepSort<uint32_t, 0, 8, 256, 16, 4, true>::describe(),
+      OnesweepSort<uint32_t, 0, 8, 256, 16, 5>::describe(),
   };
   *count = int(sizeof(table) / sizeof(table[0]));
   return table;

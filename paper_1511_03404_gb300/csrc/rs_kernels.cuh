@@ -95,6 +95,34 @@ __device__ __forceinline__ void warp_rank(const uint32_t (&dg)[ITEMS], uint32_t 
   }
 }
 
+// The same rank with digit and result in one register per item: dp[j] holds
+// the digit on entry and (digit << 16) | rank on exit (ITEMS * 32 <= 65536).
+// Every lane reads the warp's running count of its digit next to the peer
+// mask, so no shuffle is needed; only the peer group's highest lane (the one
+// whose bit is the mask's top bit) writes back, by predicated stores.
+template <int ITEMS>
+__device__ __forceinline__ void warp_rank_packed(uint32_t (&dp)[ITEMS], uint32_t* wh,
+                                                 uint32_t* mm, int lane) {
+  static_assert(ITEMS * 32 <= 65536, "ranks fit 16 bits");
+  const uint32_t bit = 1u << lane;
+  const uint32_t lt = bit - 1u;
+#pragma unroll
+  for (int j = 0; j < ITEMS; ++j) {
+    const uint32_t d = dp[j];
+    atomicOr(&mm[d], bit);
+    __syncwarp();
+    const uint32_t peers = mm[d];
+    const uint32_t before = wh[d];
+    __syncwarp();
+    if ((peers >> lane) == 1u) {  // the highest peer
+      mm[d] = 0u;
+      wh[d] = before + uint32_t(__popc(peers));
+    }
+    __syncwarp();
+    dp[j] = (d << 16) | (before + uint32_t(__popc(peers & lt)));
+  }
+}
+
 template <class K>
 __device__ __forceinline__ uint32_t digit_of(K key, uint32_t shift, uint32_t mask) {
   return static_cast<uint32_t>(key >> shift) & mask;
@@ -609,10 +637,10 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
   // ---- rank within the warp: warp w owns tile slots [w*ITEMS*32, (w+1)*ITEMS*32),
   // item j of lane l is slot w*ITEMS*32 + j*32 + l
   const uint32_t slot0 = uint32_t(warp * ITEMS * 32 + lane);
-  uint32_t dg[ITEMS], pos[ITEMS];
+  uint32_t dp[ITEMS];  // digit << 16 | rank in the warp
 #pragma unroll
-  for (int j = 0; j < ITEMS; ++j) dg[j] = digit_of(s_kin[slot0 + j * 32], t.shift, t.mask);
-  warp_rank<ITEMS>(dg, pos, s_wh + warp * RADIX, s_mm + warp * RADIX, lane);
+  for (int j = 0; j < ITEMS; ++j) dp[j] = digit_of(s_kin[slot0 + j * 32], t.shift, t.mask);
+  warp_rank_packed<ITEMS>(dp, s_wh + warp * RADIX, s_mm + warp * RADIX, lane);
   __syncthreads();
   stamp(t.trace, 2);
 
@@ -646,10 +674,12 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
 
   // ---- keys into the stage in (digit, input) order (the peer masks are done)
   K* s_out = reinterpret_cast<K*>(smem + S::OUT);
+  uint32_t pos[VB > 0 ? ITEMS : 1];  // stage slots, for the values
 #pragma unroll
   for (int j = 0; j < ITEMS; ++j) {
-    pos[j] += s_wh[warp * RADIX + dg[j]];
-    s_out[pos[j]] = s_kin[slot0 + j * 32];
+    const uint32_t p = (dp[j] & 0xffffu) + s_wh[warp * RADIX + (dp[j] >> 16)];
+    s_out[p] = s_kin[slot0 + j * 32];
+    if constexpr (VB > 0) pos[j] = p;
   }
   stamp(t.trace, 8);
 
@@ -743,9 +773,19 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
         ((tile + 1) % kGroupTiles == 0 || tile + 1 == t.tiles))
       st_relaxed(&t.ginc[lb_index<RADIX>(tile / kGroupTiles, tid)],
                  gave_up ? kFlagErr : (kFlagInc | ((excl + my_cnt) & kValueMask)));
+    // every key of digit tid goes to [pass offset + excl, ... + its count):
+    // checked here once, so that the scatters below need no per-element
+    // bound.  The past-the-end sentinels of a partial tile were counted under
+    // the largest digit; they are never written.
+    const uint32_t base = t.pass_offsets[tid] + excl;
+    const uint32_t real = my_cnt - (uint32_t(tid) == t.mask ? uint32_t(TILE) - tile_len : 0u);
+    if (!gave_up && (base > n || real > n - base)) {
+      report_error(ctrl, kDevIndex, tile);
+      gave_up = true;
+    }
     if (gave_up) s_misc[1] = 1u;
     stamp(t.trace, 9);
-    s_gbase[tid] = t.pass_offsets[tid] + excl - my_start;
+    s_gbase[tid] = base - my_start;
   }
   __syncthreads();
   if (s_misc[1]) {
@@ -778,19 +818,27 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
 
   // ---- scatter: consecutive threads take consecutive stage slots, which map
   // to consecutive output addresses inside each digit run
-  uint32_t gidx[ITEMS];
+  const bool full = tile_len == uint32_t(TILE);
+  uint32_t gidx[VB > 0 ? ITEMS : 1];  // the values' destinations
+  if (full) {
 #pragma unroll
-  for (int s = 0; s < ITEMS; ++s) {
-    const uint32_t i = uint32_t(s * THREADS + tid);
-    gidx[s] = 0xffffffffu;
-    if (i < tile_len) {
+    for (int s = 0; s < ITEMS; ++s) {
+      const uint32_t i = uint32_t(s * THREADS + tid);
       const K k = s_out[i];
       const uint32_t g = s_gbase[digit_of(k, t.shift, t.mask)] + i;
-      if (g < n) {
+      t.kdst[g] = k;
+      if constexpr (VB > 0) gidx[s] = g;
+    }
+  } else {
+#pragma unroll
+    for (int s = 0; s < ITEMS; ++s) {
+      const uint32_t i = uint32_t(s * THREADS + tid);
+      if constexpr (VB > 0) gidx[s] = 0u;
+      if (i < tile_len) {
+        const K k = s_out[i];
+        const uint32_t g = s_gbase[digit_of(k, t.shift, t.mask)] + i;
         t.kdst[g] = k;
-        gidx[s] = g;
-      } else {
-        report_error(ctrl, kDevIndex, tile);
+        if constexpr (VB > 0) gidx[s] = g;
       }
     }
   }
@@ -817,10 +865,15 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
         if (s_misc[4])
           stage_keys<K, THREADS, TILE, CG>(smem + S::KIN, t.ksrc, n, s_misc[3], &s_bar[0]);
       }
+      if (full) {
 #pragma unroll
-      for (int s = 0; s < ITEMS; ++s) {
-        const uint32_t i = uint32_t(s * THREADS + tid);
-        if (gidx[s] != 0xffffffffu) t.vdst[gidx[s]] = s_vout[i];
+        for (int s = 0; s < ITEMS; ++s) t.vdst[gidx[s]] = s_vout[s * THREADS + tid];
+      } else {
+#pragma unroll
+        for (int s = 0; s < ITEMS; ++s) {
+          const uint32_t i = uint32_t(s * THREADS + tid);
+          if (i < tile_len) t.vdst[gidx[s]] = s_vout[i];
+        }
       }
     } else {
       ok = false;

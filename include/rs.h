@@ -78,15 +78,40 @@ const char* rs_status_string(rs_status s);
 /* Library version as "major.minor.patch" (static string). */
 const char* rs_version(void);
 
+/* How the key bits are read (rs_config.key_kind). */
+typedef enum rs_key_kind {
+  RS_KEY_UNSIGNED = 0, /* unsigned integers (the paper's keys, Sec. 3) */
+  RS_KEY_SIGNED = 1,   /* two's-complement signed integers of key_bytes */
+  RS_KEY_FLOAT = 2     /* IEEE-754 binary32 (key_bytes 4) or binary64 (key_bytes 8) */
+} rs_key_kind;
+
 /*
- * Tuning parameters.  radix_bits is the digit width r of Sec. 2.6; the sorted
- * result does not depend on it.  variant selects one of the compiled tile
- * shapes (threads per CTA x keys per thread), see rs_variant_info().
- * A zero / negative field means "let the library choose" (the tuned table).
+ * Tuning parameters and key order.  radix_bits is the digit width r of
+ * Sec. 2.6; the sorted result does not depend on it.  variant selects one of
+ * the compiled tile shapes (threads per CTA x keys per thread), see
+ * rs_variant_info().  A zero / negative tuning field means "let the library
+ * choose" (the tuned table).  A zero-initialised struct sorts unsigned keys
+ * in ascending order.
+ *
+ * key_kind and descending extend the paper's unsigned LSD sort (its digit
+ * decomposition is defined on unsigned integers) by an order-preserving bit
+ * transform T applied to each key before its digits are taken, and undone
+ * on the way out; the keys returned are the caller's own bit patterns.
+ *   signed:  T flips the sign bit.
+ *   float:   T flips every bit of a negative value and the sign bit of a
+ *            non-negative one, giving the total order
+ *            -NaN < -inf < ... < -0.0 < +0.0 < ... < +inf < +NaN
+ *            (-0.0 sorts before +0.0; NaNs sort by sign and payload).
+ *   descending: T additionally inverts every bit.
+ * The sort stays stable in every mode: equal keys (equal bit patterns) keep
+ * their input order, also when descending.  begin_bit / end_bit select bits
+ * of the transformed key.
  */
 typedef struct rs_config {
   int radix_bits; /* 0: library choice; else one of the compiled widths */
   int variant;    /* -1: library choice; else an index from rs_variant_info */
+  int key_kind;   /* rs_key_kind; any other value is RS_ERR_INVALID */
+  int descending; /* 0: ascending, 1: descending; any other value is RS_ERR_INVALID */
 } rs_config;
 
 /* Number of compiled tile variants for (key_bytes, val_bytes); val_bytes 0 = keys only. */
@@ -178,9 +203,12 @@ rs_status rs_sort_keys_u32_noalloc(uint32_t* keys, uint32_t* keys_alt, size_t n,
                                    int end_bit, rs_stream_t stream, int* result_in_alt);
 
 /*
- * Generic form of the four sorts above with an explicit configuration.
- * key_bytes is 4 or 8; val_bytes is 0 (keys only) or equal to key_bytes.
- * vals / vals_alt must be NULL when val_bytes is 0.
+ * Generic form of the four sorts above with an explicit configuration
+ * (cfg may be NULL: unsigned ascending, library-chosen tuning).  key_bytes is
+ * 4 or 8; val_bytes is 0 (keys only) or equal to key_bytes.  vals / vals_alt
+ * must be NULL when val_bytes is 0.  cfg->key_kind and cfg->descending
+ * choose the key order (see rs_config); a bad value is RS_ERR_INVALID with
+ * nothing enqueued.
  */
 rs_status rs_sort(int key_bytes, int val_bytes, void* keys, void* vals, void* keys_alt,
                   void* vals_alt, size_t n, int begin_bit, int end_bit, const rs_config* cfg,

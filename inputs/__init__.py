@@ -110,6 +110,40 @@ def keys(dtype, dist: str, n: int, seed: int = 1) -> np.ndarray:
     return out
 
 
+def float_keys(dtype, n: int, seed: int = 1) -> np.ndarray:
+    """``n`` IEEE-754 keys as bit patterns (np.uint32 for binary32, np.uint64
+    for binary64): mostly finite values of both signs spread over a wide
+    range of exponents, about 1/8 special patterns (+-0, +-inf, quiet and
+    signalling NaNs of both signs, subnormals, the largest finite values),
+    and many repeated values (every fourth key repeats an earlier one)."""
+    dtype = np.dtype(dtype)
+    if dtype == np.uint32:
+        raw = mt19937(seed, 4 * n).astype(np.uint64)
+        ebits, fbits, bias = 8, 23, 127
+    elif dtype == np.uint64:
+        raw = mt19937_64(seed, 4 * n)
+        ebits, fbits, bias = 11, 52, 1023
+    else:
+        raise TypeError(f"unsupported key dtype {dtype}")
+    w = ebits + fbits + 1
+    a, b, c, d = raw[0::4], raw[1::4], raw[2::4], raw[3::4]
+    sign = (a & 1) << (w - 1)
+    exp = (bias - 40 + (a >> 1) % 81) << fbits          # 2^-40 .. 2^40
+    frac = b & ((1 << fbits) - 1)
+    out = sign | exp | frac
+    emax = ((1 << ebits) - 1) << fbits
+    specials = np.array([0, 1 << (w - 1), emax, emax | (1 << (w - 1)), emax | 1,
+                         emax | (1 << (fbits - 1)), emax | (1 << (fbits - 1)) | (1 << (w - 1)),
+                         emax | ((1 << fbits) - 1) | (1 << (w - 1)), 1, (1 << (w - 1)) | 3,
+                         emax - 1, (emax - 1) | (1 << (w - 1))], dtype=np.uint64)
+    pick = (c % 8) == 0
+    out[pick] = specials[(c[pick] >> 3) % len(specials)]
+    rep = (d % 4) == 0
+    src = (d >> 2) % np.maximum(np.arange(n, dtype=np.uint64), 1)
+    out[rep] = out[src[rep].astype(np.int64)]
+    return out.astype(dtype)
+
+
 def values(dtype, n: int) -> np.ndarray:
     """Values of a key-value workload: value[i] = i, the original index."""
     return np.arange(n, dtype=np.dtype(dtype))

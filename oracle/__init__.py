@@ -57,9 +57,12 @@ def bind(lib):
     lib.oracle_digit_offsets.argtypes = [vp, i32, i32, vp]
     lib.oracle_segmented_sort_u32.argtypes = [vp, vp, vp, u64, i32, i32, i32]
     lib.oracle_segmented_sort_u64.argtypes = [vp, vp, vp, u64, i32, i32, i32]
+    lib.oracle_order_keys_u32.argtypes = [vp, vp, u64, i32, i32]
+    lib.oracle_order_keys_u64.argtypes = [vp, vp, u64, i32, i32]
     for name in ("oracle_num_passes", "oracle_lsd_sort_u32", "oracle_lsd_sort_u64",
                  "oracle_digit_counts_u64", "oracle_digit_offsets",
-                 "oracle_segmented_sort_u32", "oracle_segmented_sort_u64"):
+                 "oracle_segmented_sort_u32", "oracle_segmented_sort_u64",
+                 "oracle_order_keys_u32", "oracle_order_keys_u64"):
         getattr(lib, name).restype = i32
     return lib
 
@@ -110,6 +113,40 @@ def lsd_sort(keys: np.ndarray, vals: np.ndarray | None = None, begin_bit: int = 
     if rc != 0:
         raise ValueError(f"oracle_lsd_sort failed with code {rc}")
     return k, v
+
+
+KEY_UNSIGNED, KEY_SIGNED, KEY_FLOAT = 0, 1, 2
+
+
+def order_keys(keys: np.ndarray, kind: int = KEY_UNSIGNED, descending: bool = False, lib=None):
+    """The unsigned order key of every bit pattern in ``keys`` (uint32 or
+    uint64 views of the caller's keys): its ascending order is the order
+    asked for (unsigned, two's-complement signed or IEEE-754 total order;
+    reversed when descending)."""
+    bits = _key_bits(keys.dtype)
+    k = np.ascontiguousarray(keys)
+    out = np.empty_like(k)
+    lib = lib or _load()
+    fn = lib.oracle_order_keys_u32 if bits == 32 else lib.oracle_order_keys_u64
+    rc = fn(_ptr(k), _ptr(out), k.size, int(kind), int(bool(descending)))
+    if rc != 0:
+        raise ValueError(f"oracle_order_keys failed with code {rc}")
+    return out
+
+
+def ordered_sort(keys: np.ndarray, vals: np.ndarray | None = None, kind: int = KEY_UNSIGNED,
+                 descending: bool = False, begin_bit: int = 0, end_bit: int | None = None,
+                 r: int = 8, lib=None):
+    """Stable sort of the bit patterns ``keys`` (uint32 / uint64 views) in the
+    order of ``kind`` / ``descending``: the LSD sort orders the order keys
+    (over their bits [begin_bit, end_bit)) and carries each element's input
+    position, which then permutes the original keys and values."""
+    n = keys.size
+    m = order_keys(keys, kind, descending, lib)
+    idx = np.arange(n, dtype=keys.dtype)
+    _, perm = lsd_sort(m, idx, begin_bit, end_bit, r, lib)
+    perm = perm.astype(np.int64)
+    return keys[perm], (None if vals is None else vals[perm])
 
 
 def digit_counts(keys: np.ndarray, begin_bit: int = 0, end_bit: int | None = None,

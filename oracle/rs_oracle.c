@@ -179,3 +179,48 @@ int oracle_segmented_sort_u64(uint64_t* keys, uint64_t* vals, const uint64_t* of
   }
   return ORACLE_OK;
 }
+
+/*
+ * Key orders beyond the paper's unsigned keys.  The order key of a w-bit
+ * pattern is an unsigned w-bit integer whose ascending order is the wanted
+ * order; the sort then orders the order keys (the LSD sort above) and
+ * carries the original patterns along.  Written from the definitions:
+ *   kind 0, unsigned: the pattern's value.
+ *   kind 1, two's complement: value v in [-2^(w-1), 2^(w-1)), order key
+ *           v + 2^(w-1).
+ *   kind 2, IEEE-754 (binary32 for w = 32, binary64 for w = 64): sign s and
+ *           the remaining bits m (exponent and fraction, which order the
+ *           magnitudes); IEEE totalOrder puts every negative pattern below
+ *           every positive one and orders negatives by decreasing m:
+ *           order key = 2^(w-1) - 1 - m if s, else 2^(w-1) + m.
+ *   descending: the order key u becomes (2^w - 1) - u.
+ */
+static uint64_t order_key(uint64_t bits, int w, int kind, int descending) {
+  const uint64_t half = (uint64_t)1 << (w - 1);
+  const uint64_t all = half + (half - 1);  /* 2^w - 1 */
+  uint64_t u;
+  if (kind == 0) {
+    u = bits;
+  } else if (kind == 1) {
+    /* patterns >= 2^(w-1) hold v = pattern - 2^w, so v + 2^(w-1) = pattern - 2^(w-1) */
+    u = bits >= half ? bits - half : bits + half;
+  } else {
+    const uint64_t m = bits & (half - 1);
+    u = (bits & half) ? half - 1 - m : half + m;
+  }
+  return descending ? all - u : u;
+}
+
+int oracle_order_keys_u32(const uint32_t* keys, uint32_t* out, uint64_t n, int kind,
+                          int descending) {
+  if ((n && (!keys || !out)) || kind < 0 || kind > 2) return ORACLE_EINVAL;
+  for (uint64_t i = 0; i < n; ++i) out[i] = (uint32_t)order_key(keys[i], 32, kind, descending);
+  return ORACLE_OK;
+}
+
+int oracle_order_keys_u64(const uint64_t* keys, uint64_t* out, uint64_t n, int kind,
+                          int descending) {
+  if ((n && (!keys || !out)) || kind < 0 || kind > 2) return ORACLE_EINVAL;
+  for (uint64_t i = 0; i < n; ++i) out[i] = order_key(keys[i], 64, kind, descending);
+  return ORACLE_OK;
+}

@@ -263,6 +263,10 @@ rs_status rs_sort(int key_bytes, int val_bytes, void* keys, void* vals, void* ke
   if (!result_in_alt || !valid_types(key_bytes, val_bytes)) return RS_ERR_INVALID;
   if (n > RS_MAX_N || begin_bit < 0 || begin_bit > end_bit || end_bit > 8 * key_bytes)
     return RS_ERR_INVALID;
+  const int key_kind = cfg ? cfg->key_kind : RS_KEY_UNSIGNED;
+  const int descending = cfg ? cfg->descending : 0;
+  if (key_kind < RS_KEY_UNSIGNED || key_kind > RS_KEY_FLOAT || (descending & ~1))
+    return RS_ERR_INVALID;
   *result_in_alt = 0;
   if (n <= 1 || begin_bit == end_bit) {  // already sorted, nothing moves
     if (ws && ws_bytes >= sizeof(Ctrl) &&
@@ -285,6 +289,8 @@ rs_status rs_sort(int key_bytes, int val_bytes, void* keys, void* vals, void* ke
   if (need > 0 && (!ws || ws_bytes < need || !aligned(ws, 256))) return RS_ERR_WORKSPACE;
   SortArgs a{keys, vals, keys_alt, vals_alt, uint32_t(n), begin_bit, end_bit, ws, ws_bytes,
              reinterpret_cast<cudaStream_t>(stream), knobs_now()};
+  a.key_kind = key_kind;
+  a.descending = descending;
   int in_alt = 0;
   const cudaError_t e = v->run(a, &in_alt);
   if (e != cudaSuccess) return RS_ERR_CUDA;

@@ -54,6 +54,54 @@ struct Knobs {
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// Order-preserving key transform for signed integers, IEEE-754 floats and
+// descending order.  The digit passes order T(k) = k ^ c ^ (f & top(k)) as
+// unsigned integers, where top(k) is all ones when the top bit of k is set;
+// the inverse is T^-1(t) = t ^ c ^ (f & top(t ^ g)).  on == 0: identity.
+//   unsigned: c = 0 (or all ones descending), f = g = 0
+//   signed:   c = sign bit (descending: all bits but the sign), f = g = 0
+//   float:    c as signed, f = all bits but the sign, g = sign bit ascending,
+//             0 descending (negative values are reversed, positive ones get
+//             the sign bit: -NaN < -inf < ... < -0 < +0 < ... < +inf < +NaN)
+template <class K>
+struct KeyXf {
+  K c, f, g;
+  uint32_t on;
+};
+
+template <class K>
+__host__ __device__ __forceinline__ K top_ones(K k) {
+  return K(0) - (k >> (8 * sizeof(K) - 1));
+}
+
+template <class K>
+__host__ __device__ __forceinline__ K xf_fwd(K k, const KeyXf<K>& x) {
+  return k ^ x.c ^ (x.f & top_ones(k));
+}
+
+template <class K>
+__host__ __device__ __forceinline__ K xf_inv(K t, const KeyXf<K>& x) {
+  return t ^ x.c ^ (x.f & top_ones(K(t ^ x.g)));
+}
+
+// kind: 0 unsigned, 1 signed (two's complement), 2 IEEE-754 float.
+template <class K>
+inline KeyXf<K> make_key_xf(int kind, int descending) {
+  const K sign = K(1) << (8 * sizeof(K) - 1);
+  KeyXf<K> x{};
+  if (kind == 0) {
+    x.c = descending ? K(~K(0)) : K(0);
+  } else {
+    x.c = descending ? K(~sign) : sign;
+    if (kind == 2) {
+      x.f = K(~sign);
+      x.g = descending ? K(0) : sign;
+    }
+  }
+  x.on = (x.c | x.f | x.g) != K(0) ? 1u : 0u;
+  return x;
+}
+
 // Word of (tile or group t, digit d) in a [t/4][radix][4] look-back array.
 template <int RADIX>
 __host__ __device__ __forceinline__ size_t lb_index(uint32_t t, uint32_t d) {

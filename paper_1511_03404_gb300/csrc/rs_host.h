@@ -23,6 +23,8 @@ struct SortArgs {
   size_t ws_bytes;
   cudaStream_t stream;
   Knobs knobs;
+  int key_kind = 0;    // 0 unsigned, 1 signed, 2 float (see KeyXf)
+  int descending = 0;
 };
 
 enum VariantKind { kOnesweep = 0, kSmall = 1, kOnesweepPersist = 2 };

@@ -194,7 +194,8 @@ template <class K, int RADIX_BITS, int THREADS, int MAXP, bool FULL>
 __global__ void __launch_bounds__(THREADS, 1)
     k_upsweep(const K* __restrict__ keys, uint32_t n, int begin_bit, int end_bit, int passes,
               uint32_t* __restrict__ counts, uint32_t* __restrict__ offsets,
-              Ctrl* __restrict__ ctrl, uint4* __restrict__ zero_base, uint64_t zero_vec4) {
+              Ctrl* __restrict__ ctrl, uint4* __restrict__ zero_base, uint64_t zero_vec4,
+              KeyXf<K> xf) {
   constexpr int RADIX = 1 << RADIX_BITS;
   constexpr int SLOTS = sizeof(K) == 4 ? 32 : 16;
   constexpr int VEC = 16 / int(sizeof(K));
@@ -220,7 +221,10 @@ __global__ void __launch_bounds__(THREADS, 1)
   for (int i = tid; i < words; i += THREADS) sh[i] = 0u;
   __syncthreads();
 
-  auto count_key = [&](K k) {
+  // XF: the digits are those of the transformed key (a compile-time switch,
+  // so that plain unsigned sorts pay nothing for it)
+  auto count_key = [&](K k, auto XF) {
+    if constexpr (decltype(XF)::value) k = xf_fwd(k, xf);
 #pragma unroll
     for (int p = 0; p < MAXP; ++p) {
       if (FULL || p < passes) {
@@ -243,29 +247,35 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (head > n) head = n;
   const uint32_t nvec = (n - head) / VEC;
   const uint32_t tail = head + nvec * VEC;
-  if (blockIdx.x == 0) {
-    if (uint32_t(tid) < head) count_key(keys[tid]);
-    if (uint32_t(tid) < n - tail) count_key(keys[tail + tid]);
-  }
   const uint4* vp = reinterpret_cast<const uint4*>(keys + head);
   const uint32_t stride = gridDim.x * THREADS;
-  for (uint32_t base = blockIdx.x * THREADS + tid; base < nvec; base += stride * UNROLL) {
-    uint4 buf[UNROLL];
-#pragma unroll
-    for (int u = 0; u < UNROLL; ++u) {
-      const uint32_t i = base + uint32_t(u) * stride;
-      if (i < nvec) buf[u] = vp[i];
+  auto count_all = [&](auto XF) {
+    if (blockIdx.x == 0) {
+      if (uint32_t(tid) < head) count_key(keys[tid], XF);
+      if (uint32_t(tid) < n - tail) count_key(keys[tail + tid], XF);
     }
+    for (uint32_t base = blockIdx.x * THREADS + tid; base < nvec; base += stride * UNROLL) {
+      uint4 buf[UNROLL];
 #pragma unroll
-    for (int u = 0; u < UNROLL; ++u) {
-      const uint32_t i = base + uint32_t(u) * stride;
-      if (i < nvec) {
-        const K* ks = reinterpret_cast<const K*>(&buf[u]);
+      for (int u = 0; u < UNROLL; ++u) {
+        const uint32_t i = base + uint32_t(u) * stride;
+        if (i < nvec) buf[u] = vp[i];
+      }
 #pragma unroll
-        for (int e = 0; e < VEC; ++e) count_key(ks[e]);
+      for (int u = 0; u < UNROLL; ++u) {
+        const uint32_t i = base + uint32_t(u) * stride;
+        if (i < nvec) {
+          const K* ks = reinterpret_cast<const K*>(&buf[u]);
+#pragma unroll
+          for (int e = 0; e < VEC; ++e) count_key(ks[e], XF);
+        }
       }
     }
-  }
+  };
+  if (xf.on)
+    count_all(std::true_type{});
+  else
+    count_all(std::false_type{});
   __syncthreads();
   // drain: one (pass, digit) per thread, summed over its slots
   for (int w = tid; w < passes * RADIX; w += THREADS) {
@@ -353,6 +363,9 @@ struct TileArgs {
   bool silent;                  // test-only: publish nothing for this tile
   bool lb_small;                // test-only: 8-word look-back windows
   uint64_t* trace;              // test-only: 16 phase stamps / counters of this tile, or null
+  KeyXf<K> xf;                  // order-preserving key transform of the sort
+  bool xin;                     // the source holds untransformed keys: apply xf on load
+  bool xout;                    // write untransformed keys (apply xf's inverse)
 };
 
 __device__ __forceinline__ uint32_t sm_id() {
@@ -632,6 +645,10 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
     }
     return false;
   }
+  if (t.xin) {  // the first pass that moves data: from here on the keys are transformed
+    for (uint32_t i = tid; i < tile_len; i += THREADS) s_kin[i] = xf_fwd(s_kin[i], t.xf);
+    __syncthreads();
+  }
   stamp(t.trace, 1);
 
   // ---- rank within the warp: warp w owns tile slots [w*ITEMS*32, (w+1)*ITEMS*32),
@@ -820,28 +837,39 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
   // to consecutive output addresses inside each digit run
   const bool full = tile_len == uint32_t(TILE);
   uint32_t gidx[VB > 0 ? ITEMS : 1];  // the values' destinations
-  if (full) {
+  // XO: the last pass that moves data writes the keys back untransformed
+  auto scatter_keys = [&](auto XO) {
+    auto out = [&](K k) {
+      if constexpr (decltype(XO)::value) return xf_inv(k, t.xf);
+      else return k;
+    };
+    if (full) {
 #pragma unroll
-    for (int s = 0; s < ITEMS; ++s) {
-      const uint32_t i = uint32_t(s * THREADS + tid);
-      const K k = s_out[i];
-      const uint32_t g = s_gbase[digit_of(k, t.shift, t.mask)] + i;
-      t.kdst[g] = k;
-      if constexpr (VB > 0) gidx[s] = g;
-    }
-  } else {
-#pragma unroll
-    for (int s = 0; s < ITEMS; ++s) {
-      const uint32_t i = uint32_t(s * THREADS + tid);
-      if constexpr (VB > 0) gidx[s] = 0u;
-      if (i < tile_len) {
+      for (int s = 0; s < ITEMS; ++s) {
+        const uint32_t i = uint32_t(s * THREADS + tid);
         const K k = s_out[i];
         const uint32_t g = s_gbase[digit_of(k, t.shift, t.mask)] + i;
-        t.kdst[g] = k;
+        t.kdst[g] = out(k);
         if constexpr (VB > 0) gidx[s] = g;
       }
+    } else {
+#pragma unroll
+      for (int s = 0; s < ITEMS; ++s) {
+        const uint32_t i = uint32_t(s * THREADS + tid);
+        if constexpr (VB > 0) gidx[s] = 0u;
+        if (i < tile_len) {
+          const K k = s_out[i];
+          const uint32_t g = s_gbase[digit_of(k, t.shift, t.mask)] + i;
+          t.kdst[g] = out(k);
+          if constexpr (VB > 0) gidx[s] = g;
+        }
+      }
     }
-  }
+  };
+  if (t.xout)
+    scatter_keys(std::true_type{});
+  else
+    scatter_keys(std::false_type{});
   stamp(t.trace, 5);
   bool ok = true;
   if constexpr (VB > 0) {
@@ -898,7 +926,7 @@ __global__ void __launch_bounds__(THREADS, MINB)
                ValT<VB>* __restrict__ v1, uint32_t n, int pass, uint32_t shift, uint32_t mask,
                const uint32_t* __restrict__ pass_offsets, uint32_t* __restrict__ status,
                uint32_t* __restrict__ gagg, uint32_t* __restrict__ ginc, uint32_t tiles,
-               Ctrl* __restrict__ ctrl, Knobs knobs) {
+               Ctrl* __restrict__ ctrl, Knobs knobs, KeyXf<K> xf) {
   using S = OnesweepSmem<K, VB, RADIX_BITS, THREADS, ITEMS>;
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t* s_misc = reinterpret_cast<uint32_t*>(smem + S::MISC);
@@ -932,6 +960,9 @@ __global__ void __launch_bounds__(THREADS, MINB)
   t.trace = (knobs.trace != nullptr && pass == knobs.trace_pass && t.tile < knobs.trace_tiles)
                 ? knobs.trace + size_t(t.tile) * 16
                 : nullptr;
+  t.xf = xf;
+  t.xin = xf.on && pass == __ffs(int(exec)) - 1;  // first and last pass that move data
+  t.xout = xf.on && pass == 31 - __clz(exec);
   onesweep_tile<K, VB, RADIX_BITS, THREADS, ITEMS, false>(t, ctrl, knobs.timeout_ns, smem);
 }
 
@@ -947,7 +978,7 @@ __global__ void __launch_bounds__(THREADS, MINB)
                        uint32_t mask, const uint32_t* __restrict__ pass_offsets,
                        uint32_t* __restrict__ status, uint32_t* __restrict__ gagg,
                        uint32_t* __restrict__ ginc, uint32_t tiles, Ctrl* __restrict__ ctrl,
-                       Knobs knobs) {
+                       Knobs knobs, KeyXf<K> xf) {
   using S = OnesweepSmem<K, VB, RADIX_BITS, THREADS, ITEMS>;
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t* s_misc = reinterpret_cast<uint32_t*>(smem + S::MISC);
@@ -979,6 +1010,9 @@ __global__ void __launch_bounds__(THREADS, MINB)
   t.ginc = ginc;
   t.tiles = tiles;
   t.lb_small = knobs.lb_small != 0;
+  t.xf = xf;
+  t.xin = xf.on && pass == __ffs(int(exec)) - 1;  // first and last pass that move data
+  t.xout = xf.on && pass == 31 - __clz(exec);
   uint32_t tile = s_misc[3];
   if (tile < tiles && s_misc[2] == 0u)
     stage_keys<K, THREADS, S::TILE, false>(smem + S::KIN, t.ksrc, n, tile, &s_bar[0]);
@@ -1038,7 +1072,7 @@ struct SmallSmem {
 template <class K, int VB, int RADIX_BITS, int THREADS, int ITEMS>
 __device__ __forceinline__ void cta_sort(const K* kin, const ValT<VB>* vin, K* kout,
                                          ValT<VB>* vout, uint32_t len, int begin_bit,
-                                         int end_bit, unsigned char* smem) {
+                                         int end_bit, unsigned char* smem, const KeyXf<K>& xf) {
   using V = ValT<VB>;
   using S = SmallSmem<K, VB, RADIX_BITS, THREADS, ITEMS>;
   constexpr int RADIX = S::RADIX, WARPS = S::WARPS;
@@ -1054,7 +1088,8 @@ __device__ __forceinline__ void cta_sort(const K* kin, const ValT<VB>* vin, K* k
 #pragma unroll
   for (int j = 0; j < ITEMS; ++j) {
     const uint32_t i = slot0 + j * 32;
-    key[j] = i < len ? kin[i] : ~K(0);  // past the end: largest digit in every pass
+    // past the end: largest digit in every pass
+    key[j] = i < len ? (xf.on ? xf_fwd(kin[i], xf) : kin[i]) : ~K(0);
     if constexpr (VB > 0) val[j] = i < len ? vin[i] : V(0);
   }
   for (int lo = begin_bit; lo < end_bit; lo += RADIX_BITS) {
@@ -1105,7 +1140,7 @@ __device__ __forceinline__ void cta_sort(const K* kin, const ValT<VB>* vin, K* k
   for (int j = 0; j < ITEMS; ++j) {
     const uint32_t i = slot0 + j * 32;
     if (i < len) {
-      kout[i] = key[j];
+      kout[i] = xf.on ? xf_inv(key[j], xf) : key[j];
       if constexpr (VB > 0) vout[i] = val[j];
     }
   }
@@ -1115,14 +1150,15 @@ __device__ __forceinline__ void cta_sort(const K* kin, const ValT<VB>* vin, K* k
 // resets so that a later status read reports this call.
 template <class K, int VB, int RADIX_BITS, int THREADS, int ITEMS>
 __global__ void __launch_bounds__(THREADS, 1)
-    k_small_sort(K* keys, ValT<VB>* vals, uint32_t n, int begin_bit, int end_bit, Ctrl* ctrl) {
+    k_small_sort(K* keys, ValT<VB>* vals, uint32_t n, int begin_bit, int end_bit, Ctrl* ctrl,
+                 KeyXf<K> xf) {
   extern __shared__ __align__(16) unsigned char smem[];
   if (ctrl != nullptr && threadIdx.x == 0) {
     ctrl->error = 0u;
     ctrl->error_info = 0u;
   }
   cta_sort<K, VB, RADIX_BITS, THREADS, ITEMS>(keys, vals, keys, vals, n, begin_bit, end_bit,
-                                              smem);
+                                              smem, xf);
 }
 
 }  // namespace rs

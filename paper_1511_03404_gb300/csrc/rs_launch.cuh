@@ -49,7 +49,8 @@ struct OnesweepSort {
     kern<<<grid, UP_THREADS, smem, a.stream>>>(
         static_cast<const K*>(a.keys), a.n, a.begin_bit, a.end_bit, passes,
         reinterpret_cast<uint32_t*>(ws + L.counts), reinterpret_cast<uint32_t*>(ws + L.offsets),
-        ctrl, reinterpret_cast<uint4*>(ws + L.status), zero_vec4);
+        ctrl, reinterpret_cast<uint4*>(ws + L.status), zero_vec4,
+        make_key_xf<K>(a.key_kind, a.descending));
     e = cudaGetLastError();
     prof_after(a.stream, 0, double(a.n) * sizeof(K));
     return e;
@@ -75,6 +76,7 @@ struct OnesweepSort {
     const unsigned grid =
         PERSIST ? unsigned(std::min<size_t>(nt, size_t(device_info().sms) * occ)) : unsigned(nt);
     const double bytes = 2.0 * double(a.n) * double(sizeof(K) + VB);
+    const KeyXf<K> xf = make_key_xf<K>(a.key_kind, a.descending);
     for (int p = 0; p < passes; ++p) {
       const int lo = a.begin_bit + p * R;
       const int width = std::min(R, a.end_bit - lo);
@@ -87,7 +89,7 @@ struct OnesweepSort {
           reinterpret_cast<uint32_t*>(ws + L.status) + size_t(p) * L.tiles * RADIX,
           reinterpret_cast<uint32_t*>(ws + L.gagg) + size_t(p) * L.groups * RADIX,
           reinterpret_cast<uint32_t*>(ws + L.ginc) + size_t(p) * L.groups * RADIX, uint32_t(nt),
-          ctrl, a.knobs);
+          ctrl, a.knobs, xf);
       e = cudaGetLastError();
       prof_after(a.stream, 1, bytes, slot, p);
       if (e != cudaSuccess) return e;
@@ -134,7 +136,8 @@ struct SmallSort {
     Ctrl* ctrl = (a.ws != nullptr && a.ws_bytes >= sizeof(Ctrl)) ? static_cast<Ctrl*>(a.ws)
                                                                   : nullptr;
     kern<<<1, THREADS, S::BYTES, a.stream>>>(static_cast<K*>(a.keys), static_cast<V*>(a.vals),
-                                             a.n, a.begin_bit, a.end_bit, ctrl);
+                                             a.n, a.begin_bit, a.end_bit, ctrl,
+                                             make_key_xf<K>(a.key_kind, a.descending));
     const cudaError_t e = cudaGetLastError();
     prof_after(a.stream, 2, 2.0 * double(a.n) * double(sizeof(K) + VB));
     return e;

@@ -326,7 +326,7 @@ __global__ void __launch_bounds__(THREADS, 2)
       const uint64_t b = a.off[s];
       const uint32_t len = uint32_t(a.off[s + 1] - b);
       cta_sort<K, VB, RADIX_BITS, THREADS, ITEMS>(k0 + b, v0 + b, kout + b, vout + b, len,
-                                                  a.begin_bit, a.end_bit, smem);
+                                                  a.begin_bit, a.end_bit, smem, KeyXf<K>{});
     } else {
       // ---- one tile of one pass of a long segment
       const uint32_t q = item - q_pass;
@@ -371,6 +371,9 @@ __global__ void __launch_bounds__(THREADS, 2)
         t.silent = false;
         t.trace = nullptr;
         t.lb_small = false;
+        t.xf = KeyXf<K>{};
+        t.xin = false;
+        t.xout = false;
         onesweep_tile<K, VB, RADIX_BITS, THREADS, ITEMS, true>(t, ctrl, a.knobs.timeout_ns,
                                                                smem);
         __threadfence();

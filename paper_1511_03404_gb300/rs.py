@@ -44,7 +44,8 @@ class RsError(RuntimeError):
 
 
 class rs_config(ctypes.Structure):
-    _fields_ = [("radix_bits", ctypes.c_int), ("variant", ctypes.c_int)]
+    _fields_ = [("radix_bits", ctypes.c_int), ("variant", ctypes.c_int),
+                ("key_kind", ctypes.c_int), ("descending", ctypes.c_int)]
 
 
 class rs_request(ctypes.Structure):
@@ -181,10 +182,13 @@ def rs_variant_info(key_bytes: int, val_bytes: int, index: int):
             "max_n": mx.value}
 
 
-def _cfg(radix_bits=0, variant=-1):
-    if radix_bits == 0 and variant < 0:
+RS_KEY_UNSIGNED, RS_KEY_SIGNED, RS_KEY_FLOAT = range(3)
+
+
+def _cfg(radix_bits=0, variant=-1, key_kind=RS_KEY_UNSIGNED, descending=False):
+    if radix_bits == 0 and variant < 0 and key_kind == RS_KEY_UNSIGNED and not descending:
         return None
-    return ctypes.byref(rs_config(radix_bits, variant))
+    return ctypes.byref(rs_config(radix_bits, variant, key_kind, int(descending)))
 
 
 def rs_workspace_bytes(key_bytes, val_bytes, n, begin_bit, end_bit, radix_bits=0, variant=-1):
@@ -233,11 +237,12 @@ def rs_sort_keys_u32_noalloc(keys, keys_alt, n, begin_bit, end_bit, stream):
 
 
 def rs_sort(key_bytes, val_bytes, keys, vals, keys_alt, vals_alt, n, begin_bit, end_bit, ws,
-            ws_bytes, stream, radix_bits=0, variant=-1):
+            ws_bytes, stream, radix_bits=0, variant=-1, key_kind=RS_KEY_UNSIGNED,
+            descending=False):
     r = _out_int()
     st = load().rs_sort(key_bytes, val_bytes, keys, vals, keys_alt, vals_alt, n, begin_bit,
-                        end_bit, _cfg(radix_bits, variant), ws, ws_bytes, stream,
-                        ctypes.byref(r))
+                        end_bit, _cfg(radix_bits, variant, key_kind, descending), ws, ws_bytes,
+                        stream, ctypes.byref(r))
     return st, r.value
 
 
@@ -342,14 +347,21 @@ def _stream_handle(stream=None) -> int:
     return s.cuda_stream
 
 
-_KEY_BYTES = {"uint32": 4, "int32": 4, "uint64": 8, "int64": 8}
+# dtype name -> (bytes, key kind)
+_KEY_TYPES = {"uint32": (4, RS_KEY_UNSIGNED), "int32": (4, RS_KEY_SIGNED),
+              "uint64": (8, RS_KEY_UNSIGNED), "int64": (8, RS_KEY_SIGNED),
+              "float32": (4, RS_KEY_FLOAT), "float64": (8, RS_KEY_FLOAT)}
+
+
+def _key_type(t):
+    name = str(t.dtype).replace("torch.", "")
+    if name not in _KEY_TYPES:
+        raise TypeError(f"expected a 32- or 64-bit integer or float tensor, got {t.dtype}")
+    return _KEY_TYPES[name]
 
 
 def _key_bytes(t) -> int:
-    name = str(t.dtype).replace("torch.", "")
-    if name not in _KEY_BYTES:
-        raise TypeError(f"keys must be a 32- or 64-bit integer tensor, got {t.dtype}")
-    return _KEY_BYTES[name]
+    return _key_type(t)[0]
 
 
 def workspace(key_bytes, val_bytes, n, begin_bit=0, end_bit=None, radix_bits=0, variant=-1,
@@ -364,17 +376,22 @@ def workspace(key_bytes, val_bytes, n, begin_bit=0, end_bit=None, radix_bits=0, 
 
 
 def sort(keys, vals=None, begin_bit=0, end_bit=None, radix_bits=0, variant=-1, stream=None,
-         ws=None, alt=None):
-    """Sort contiguous device tensors in place (ascending unsigned, stable).
+         ws=None, alt=None, descending=False, key_kind=None):
+    """Sort contiguous device tensors in place (stable).
 
-    ``keys`` (and ``vals``, same dtype width) are overwritten with the sorted
-    sequence; signed dtypes are sorted as their unsigned bit patterns.
+    ``keys`` (and ``vals``, any dtype of the keys' width) are overwritten with
+    the sorted sequence.  The key order follows the dtype: unsigned, signed
+    (int32 / int64) or IEEE float (float32 / float64, -0.0 before +0.0, NaNs
+    by sign at the ends); ``key_kind`` overrides it (for instance
+    ``RS_KEY_UNSIGNED`` to sort int32 storage as unsigned bit patterns).
     Returns ``(keys, vals)``.
     """
     torch = _torch()
     if not keys.is_cuda or not keys.is_contiguous():
         raise ValueError("keys must be a contiguous CUDA tensor")
-    kb = _key_bytes(keys)
+    kb, kind = _key_type(keys)
+    if key_kind is not None:
+        kind = key_kind
     vb = 0
     if vals is not None:
         vb = _key_bytes(vals)
@@ -392,7 +409,7 @@ def sort(keys, vals=None, begin_bit=0, end_bit=None, radix_bits=0, variant=-1, s
     st, in_alt = rs_sort(kb, vb, keys.data_ptr(), vals.data_ptr() if vals is not None else None,
                          ka.data_ptr(), va.data_ptr() if va is not None else None, n, begin_bit,
                          end_bit, ws.data_ptr(), ws.numel(), _stream_handle(stream), radix_bits,
-                         variant)
+                         variant, kind, descending)
     check(st, "rs_sort")
     if in_alt:
         keys.copy_(ka)

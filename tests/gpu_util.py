@@ -20,7 +20,7 @@ def from_dev(t, dtype) -> np.ndarray:
 
 def sort_via_abi(torch, keys: np.ndarray, vals: np.ndarray | None = None, begin_bit=0,
                  end_bit=None, radix_bits=0, variant=-1, api="generic", stream=None,
-                 offset_elems=0, check_status=True):
+                 offset_elems=0, check_status=True, key_kind=0, descending=False):
     """Sort host arrays on the GPU through the C ABI; returns host arrays.
 
     ``offset_elems`` places the arrays that many elements into larger device
@@ -47,9 +47,10 @@ def sort_via_abi(torch, keys: np.ndarray, vals: np.ndarray | None = None, begin_
     s = stream if stream is not None else torch.cuda.current_stream()
     h = s.cuda_stream
     ptr = lambda t: None if t is None else t.data_ptr()  # noqa: E731
-    if api == "generic" or radix_bits or variant >= 0:
+    if api == "generic" or radix_bits or variant >= 0 or key_kind or descending:
         st, in_alt = rs.rs_sort(kb, vb, ptr(dk), ptr(dv), ptr(ka), ptr(va), n, begin_bit,
-                                end_bit, ws.data_ptr(), ws.numel(), h, radix_bits, variant)
+                                end_bit, ws.data_ptr(), ws.numel(), h, radix_bits, variant,
+                                key_kind, descending)
     else:
         fn = {(4, 0): rs.rs_sort_keys_u32, (8, 0): rs.rs_sort_keys_u64,
               (4, 4): rs.rs_sort_pairs_u32, (8, 8): rs.rs_sort_pairs_u64}[(kb, vb)]

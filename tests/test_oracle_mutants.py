@@ -2,7 +2,8 @@
 
 Each mutant is a plausible slip in the LSD counting sort of arXiv 1511.03404
 Sec. 2.6 (unstable scatter, wrong digit order, wrong digit field, wrong
-prefix, values not moved with their keys, a pass dropped).  The mutated
+prefix, values not moved with their keys, a pass dropped), or in the order
+keys of signed, float and descending sorts.  The mutated
 source is compiled into a temporary library (on the CPU only) and the pin
 checks of ``tests/test_oracle.py`` run against it in a child process; every
 mutant must fail at least one of them.  The unmodified source must pass.
@@ -31,6 +32,12 @@ MUTANTS = {
         "for (uint64_t v = radix; v-- > 0;) {\n    start[v] = run;"),
     "values_left_behind": ("if (val) val_out[dst] = val[i];", "if (val) val_out[dst] = val[dst];"),
     "one_pass_short": ("return (end_bit - begin_bit + r - 1) / r;", "return (end_bit - begin_bit) / r;"),
+    # key orders beyond unsigned keys
+    "signed_read_as_unsigned": ("u = bits >= half ? bits - half : bits + half;", "u = bits;"),
+    "float_sign_flip_only": ("u = (bits & half) ? half - 1 - m : half + m;", "u = bits ^ half;"),
+    "float_zero_signs_merged": ("u = (bits & half) ? half - 1 - m : half + m;",
+                                "u = (bits & half) ? half - m : half + m;"),
+    "descending_ignored": ("return descending ? all - u : u;", "return u;"),
 }
 
 CHILD = r"""
@@ -77,6 +84,9 @@ check("library_sort", library_sort)
 check("brute", brute)
 check("bit_ranges", bit_ranges)
 check("invariants", invariants)
+import test_oracle_keyorder as KO
+for name, pin in KO.PINS.items():
+    check("keyorder_" + name, lambda: pin(lib))
 print(",".join(fails))
 """
 

@@ -47,7 +47,11 @@ L2_FLUSH_BYTES = 256 << 20
 # dram__bytes_write.sum of pass 0 of a 2^26-pair sort), keyed by the hash of the
 # kernel sources it was taken on; when they change the figure no longer applies
 # and traffic is null.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    "b5f8ead6784f0ee5": {"bytes_per_launch": 1097219904, "n": 1 << 26,
+                         "kernel": "k_onesweep_persist<u32,4,8,256,16,4>",
+                         "summary": "profiles/traffic_onesweep_kv32_2p26.md"},
+}
 
 ONESWEEP_SOURCES = ("rs_kernels.cuh", "rs_common.h", "rs_launch.cuh", "rs_inst_kv32.cu")
 

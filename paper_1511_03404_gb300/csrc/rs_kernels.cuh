@@ -112,14 +112,15 @@ __device__ __forceinline__ void warp_rank_packed(uint32_t (&dp)[ITEMS], uint32_t
     atomicOr(&mm[d], bit);
     __syncwarp();
     const uint32_t peers = mm[d];
-    const uint32_t before = wh[d];
     __syncwarp();
-    if ((peers >> lane) == 1u) {  // the highest peer
+    const int leader = 31 - __clz(peers);
+    uint32_t before = 0u;
+    if (lane == leader) {
       mm[d] = 0u;
-      wh[d] = before + uint32_t(__popc(peers));
+      before = atomicAdd(&wh[d], uint32_t(__popc(peers)));
     }
     __syncwarp();
-    dp[j] = (d << 16) | (before + uint32_t(__popc(peers & lt)));
+    dp[j] = (d << 16) | (__shfl_sync(kFull, before, leader) + uint32_t(__popc(peers & lt)));
   }
 }
 

@@ -190,3 +190,80 @@ def segmented_sort(keys: np.ndarray, vals: np.ndarray | None, offsets: np.ndarra
     if rc != 0:
         raise ValueError(f"oracle_segmented_sort failed with code {rc}")
     return k, v
+
+
+def sample_partition(keys: np.ndarray, vals: np.ndarray, block: int, samples: int, buckets: int,
+                     lib=None):
+    """Deterministic regular-sampling partition of sample sort (Sec. 2.7, the
+    variant of Dehne et al.), step by step:
+
+    1. split the input into blocks of ``block`` elements and sort each block
+       stably (the LSD sort above);
+    2. from each sorted block of length L take ``samples`` equidistant
+       elements, at positions floor(j L / samples), j = 0 .. samples - 1
+       (the block's minimum and then every (L / samples)-th element);
+    3. sort all samples; the splitters are the sorted samples at positions
+       floor((k + 1) M / buckets), k = 0 .. buckets - 2 (M samples in all);
+    4. an element x belongs to bucket b = the number of splitters < x, so
+       equal keys always share a bucket;
+    5. bucket b collects, block after block, each sorted block's run of
+       bucket-b elements.
+
+    Returns ``(keys, vals, bucket_offsets[buckets + 1], splitters)``; keys and
+    values are the partitioned copies (uint32)."""
+    n = keys.size
+    k = np.ascontiguousarray(keys).copy()
+    v = np.ascontiguousarray(vals).copy()
+    nblk = (n + block - 1) // block
+    for i in range(nblk):
+        a, b = i * block, min(n, (i + 1) * block)
+        k[a:b], v[a:b] = lsd_sort(k[a:b], v[a:b], lib=lib)
+    picked = []
+    for i in range(nblk):
+        a, b = i * block, min(n, (i + 1) * block)
+        L = b - a
+        for j in range(samples):
+            picked.append(k[a + (j * L) // samples])
+    sample = np.array(picked, dtype=keys.dtype)
+    sample, _ = lsd_sort(sample, None, lib=lib)
+    M = sample.size
+    splitters = np.array([sample[((q + 1) * M) // buckets] for q in range(buckets - 1)],
+                         dtype=keys.dtype) if M else np.zeros(0, dtype=keys.dtype)
+    counts = np.zeros((buckets, nblk), dtype=np.int64)
+    runs = []
+    for i in range(nblk):
+        a, b = i * block, min(n, (i + 1) * block)
+        bucket = np.searchsorted(splitters, k[a:b], side="left")  # splitters < x
+        counts[:, i] = np.bincount(bucket, minlength=buckets)
+        runs.append(bucket)
+    offsets = np.zeros(buckets + 1, dtype=np.uint64)
+    offsets[1:] = np.cumsum(counts.sum(axis=1))
+    ok = np.empty_like(k)
+    ov = np.empty_like(v)
+    for q in range(buckets):
+        pos = int(offsets[q])
+        for i in range(nblk):
+            a = i * block
+            sel = np.nonzero(runs[i] == q)[0]
+            ok[pos:pos + sel.size] = k[a + sel]
+            ov[pos:pos + sel.size] = v[a + sel]
+            pos += sel.size
+    return ok, ov, offsets, splitters
+
+
+def sample_sort(keys: np.ndarray, vals: np.ndarray, block: int, samples: int, buckets: int,
+                lib=None):
+    """Sample sort: the partition above, then every bucket sorted by the LSD
+    sort (the "alternative sort" of Sec. 2.7)."""
+    k, v, off, _ = sample_partition(keys, vals, block, samples, buckets, lib)
+    return segmented_sort(k, v, off) if lib is None else _segmented_with(lib, k, v, off)
+
+
+def _segmented_with(lib, k, v, off):
+    fn = lib.oracle_segmented_sort_u32 if _key_bits(k.dtype) == 32 else lib.oracle_segmented_sort_u64
+    k = k.copy(); v = v.copy()
+    rc = fn(_ptr(k), _ptr(v), _ptr(np.ascontiguousarray(off, dtype=np.uint64)), len(off) - 1, 0,
+            _key_bits(k.dtype), 8)
+    if rc != 0:
+        raise ValueError(f"oracle_segmented_sort failed with code {rc}")
+    return k, v

@@ -215,6 +215,54 @@ rs_status rs_sort(int key_bytes, int val_bytes, void* keys, void* vals, void* ke
                   void* ws, size_t ws_bytes, rs_stream_t stream, int* result_in_alt);
 
 /*
+ * Sample sort (Sec. 2.7), the regular-sampling variant after Dehne et al.,
+ * as an MSD partition front end for 32-bit key-value pairs.
+ *   1. The input is cut into blocks of 4096 pairs and every block is sorted
+ *      stably, in place in keys / vals (they are overwritten).
+ *   2. From each sorted block of L pairs, `samples` keys are taken at
+ *      positions floor(j * L / samples), j = 0 .. samples - 1.
+ *   3. The samples are sorted; splitter q (q = 0 .. buckets - 2) is the
+ *      sorted sample at rank floor((q + 1) * M / buckets), M samples in all.
+ *   4. A pair with key x belongs to bucket q = the number of splitters < x
+ *      (equal keys always share a bucket).
+ *   5. keys_out / vals_out receive the buckets in order; bucket q holds,
+ *      block after block, each block's run of bucket-q pairs, so every key
+ *      of bucket q lies in (splitter[q-1], splitter[q]] and pairs of equal
+ *      keys keep their input order.
+ *   keys, vals          [n] u32 device; overwritten (block-sorted)
+ *   keys_out, vals_out  [n] u32 device, distinct from keys / vals
+ *   samples             1 .. 4096 samples per block
+ *   buckets             2 .. 4096 buckets (nblocks * buckets < 2^32)
+ *   d_bucket_offsets    [buckets + 1] u64 device: bucket q is
+ *                       [off[q], off[q+1]) of keys_out
+ *   d_splitters         [buckets - 1] u32 device, or NULL
+ *   ws                  device workspace of rs_sample_workspace_bytes() bytes,
+ *                       256-byte aligned
+ * Asynchronous on `stream`.  Bad sizes, pointers or alignment:
+ * RS_ERR_INVALID with nothing enqueued; workspace too small:
+ * RS_ERR_WORKSPACE.  Device-side status words of the sorts it runs are
+ * read with rs_workspace_status on the segmented part of ws (not needed in
+ * normal use).
+ */
+rs_status rs_sample_workspace_bytes(size_t n, int samples, int buckets, size_t* bytes);
+rs_status rs_sample_partition_pairs_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_out,
+                                        uint32_t* vals_out, size_t n, int samples, int buckets,
+                                        uint64_t* d_bucket_offsets, uint32_t* d_splitters,
+                                        void* ws, size_t ws_bytes, rs_stream_t stream);
+
+/*
+ * Sample sort of 32-bit pairs: the partition above, then every bucket sorted
+ * by the LSD radix sort (one batched segmented sort, Sec. 2.7's "alternative
+ * sort").  The result equals rs_sort_pairs_u32's (stable, ascending);
+ * *result_in_alt = 1 when it is in keys_out / vals_out (always, for n > 0),
+ * 0 when in keys / vals.  Arguments as for rs_sample_partition_pairs_u32.
+ */
+rs_status rs_sample_sort_pairs_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_out,
+                                   uint32_t* vals_out, size_t n, int samples, int buckets,
+                                   uint64_t* d_bucket_offsets, void* ws, size_t ws_bytes,
+                                   rs_stream_t stream, int* result_in_alt);
+
+/*
  * Digit histograms and their exclusive scans, the first two steps of each
  * counting sort of Sec. 2.6, for every digit pass at once.
  *   keys         [n] device keys of key_bytes (4 or 8); not modified

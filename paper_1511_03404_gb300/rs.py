@@ -86,6 +86,10 @@ _SIGS = {
     "rs_segmented_sort_pairs": ([_vp, _vp, _vp, _vp, _sz, _vp, _sz, _i, _i, _vp, _sz, _vp, _vp],
                                 _i),
     "rs_segmented_workspace_bytes": ([_sz, _sz, _i, _i, _vp], _i),
+    "rs_sample_workspace_bytes": ([_sz, _i, _i, _vp], _i),
+    "rs_sample_partition_pairs_u32": ([_vp, _vp, _vp, _vp, _sz, _i, _i, _vp, _vp, _vp, _sz, _vp],
+                                      _i),
+    "rs_sample_sort_pairs_u32": ([_vp, _vp, _vp, _vp, _sz, _i, _i, _vp, _vp, _sz, _vp, _vp], _i),
     "rs_server_create": ([_sz, _i, _vp], _i),
     "rs_server_destroy": ([_vp], _i),
     "rs_submit": ([_vp, _vp, _vp], _i),
@@ -265,6 +269,27 @@ def rs_segmented_workspace_bytes(n, n_seg, begin_bit=0, end_bit=32):
     out = ctypes.c_size_t()
     st = load().rs_segmented_workspace_bytes(n, n_seg, begin_bit, end_bit, ctypes.byref(out))
     return st, out.value
+
+
+def rs_sample_workspace_bytes(n, samples, buckets):
+    out = ctypes.c_size_t()
+    st = load().rs_sample_workspace_bytes(n, samples, buckets, ctypes.byref(out))
+    return st, out.value
+
+
+def rs_sample_partition_pairs_u32(keys, vals, keys_out, vals_out, n, samples, buckets,
+                                  d_bucket_offsets, d_splitters, ws, ws_bytes, stream):
+    return load().rs_sample_partition_pairs_u32(keys, vals, keys_out, vals_out, n, samples,
+                                                buckets, d_bucket_offsets, d_splitters, ws,
+                                                ws_bytes, stream)
+
+
+def rs_sample_sort_pairs_u32(keys, vals, keys_out, vals_out, n, samples, buckets,
+                             d_bucket_offsets, ws, ws_bytes, stream):
+    r = _out_int()
+    st = load().rs_sample_sort_pairs_u32(keys, vals, keys_out, vals_out, n, samples, buckets,
+                                         d_bucket_offsets, ws, ws_bytes, stream, ctypes.byref(r))
+    return st, r.value
 
 
 def rs_workspace_status(ws, stream):

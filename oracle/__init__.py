@@ -267,3 +267,19 @@ def _segmented_with(lib, k, v, off):
     if rc != 0:
         raise ValueError(f"oracle_segmented_sort failed with code {rc}")
     return k, v
+
+
+def sort_wide(keys128: np.ndarray, vals: np.ndarray | None = None, lib=None):
+    """Stable ascending sort of 128-bit unsigned keys given as an (n, 2)
+    uint64 array of (low word, high word): the key's value is
+    low + 2^64 * high.  Written out as the LSD sort's definition over two
+    64-bit digits: a stable sort by the low word, then a stable sort by the
+    high word, each carrying the input positions (the LSD sort above)."""
+    k = np.ascontiguousarray(keys128, dtype=np.uint64).reshape(-1, 2)
+    n = k.shape[0]
+    idx = np.arange(n, dtype=np.uint64)
+    _, p1 = lsd_sort(k[:, 0].copy(), idx, lib=lib)          # by the low word
+    p1 = p1.astype(np.int64)
+    _, p2 = lsd_sort(k[p1, 1].copy(), idx.copy(), lib=lib)  # then by the high word, stably
+    perm = p1[p2.astype(np.int64)]
+    return k[perm].copy(), (None if vals is None else vals[perm].copy())

@@ -263,6 +263,32 @@ rs_status rs_sample_sort_pairs_u32(uint32_t* keys, uint32_t* vals, uint32_t* key
                                    rs_stream_t stream, int* result_in_alt);
 
 /*
+ * Merge sort (Sec. 2.4; the parallel merge sort of Satish et al.): a stable
+ * comparison sort, ascending, for keys the radix passes do not take as well
+ * as for 32- and 64-bit keys.
+ *   key_bytes 4 (u32), 8 (u64) or 16: a 128-bit unsigned key stored as two
+ *             little-endian u64 words (value = word0 + 2^64 * word1), array
+ *             16-byte aligned
+ *   val_bytes 0, or the key width for 4 / 8-byte keys, or 8 for 16-byte keys
+ *   keys, vals, keys_alt, vals_alt  [n] device arrays (double buffer); the
+ *             result ends in keys / vals (*result_in_alt = 0) or in the
+ *             alternates (1): the parity of the number of merge passes,
+ *             ceil(log2(ceil(n / 2048)))
+ *   ws        device workspace of rs_merge_workspace_bytes() bytes, 256-byte
+ *             aligned (the merge-path split of every output tile)
+ * Tiles of 2048 elements are sorted inside one CTA each, then runs are merged
+ * pairwise, each CTA producing one tile of the output from the two input
+ * ranges a merge-path search delimits.  Equal keys keep their input order.
+ * Asynchronous on `stream`.  Bad types, sizes, pointers or alignment:
+ * RS_ERR_INVALID; workspace too small: RS_ERR_WORKSPACE; both with nothing
+ * enqueued.
+ */
+rs_status rs_merge_workspace_bytes(int key_bytes, int val_bytes, size_t n, size_t* bytes);
+rs_status rs_merge_sort(int key_bytes, int val_bytes, void* keys, void* vals, void* keys_alt,
+                        void* vals_alt, size_t n, void* ws, size_t ws_bytes, rs_stream_t stream,
+                        int* result_in_alt);
+
+/*
  * Digit histograms and their exclusive scans, the first two steps of each
  * counting sort of Sec. 2.6, for every digit pass at once.
  *   keys         [n] device keys of key_bytes (4 or 8); not modified
@@ -388,7 +414,8 @@ typedef enum rs_kernel_kind {
   RS_KERNEL_ONESWEEP = 1, /* one digit pass: rank, look-back, stable scatter */
   RS_KERNEL_SMALL = 2,   /* whole array sorted by one CTA in shared memory */
   RS_KERNEL_SEGMENTED = 3, /* batched segments */
-  RS_KERNEL_KINDS = 4
+  RS_KERNEL_MERGE = 4,   /* merge sort: tile sort or one merge pass */
+  RS_KERNEL_KINDS = 5
 } rs_kernel_kind;
 
 /*

@@ -29,9 +29,10 @@ RS_ERR_CANCELLED = 8
 RS_ERR_NOT_FOUND = 9
 RS_MAX_N = (1 << 30) - 1
 
-RS_KERNEL_UPSWEEP, RS_KERNEL_ONESWEEP, RS_KERNEL_SMALL, RS_KERNEL_SEGMENTED = range(4)
-RS_KERNEL_KINDS = 4
-KERNEL_NAMES = ("upsweep", "onesweep", "small", "segmented")
+RS_KERNEL_UPSWEEP, RS_KERNEL_ONESWEEP, RS_KERNEL_SMALL, RS_KERNEL_SEGMENTED, RS_KERNEL_MERGE = \
+    range(5)
+RS_KERNEL_KINDS = 5
+KERNEL_NAMES = ("upsweep", "onesweep", "small", "segmented", "merge")
 
 (RS_DEBUG_TIMEOUT_NS, RS_DEBUG_DROP_PUBLISH_TILE, RS_DEBUG_DROP_PUBLISH_PASS, RS_DEBUG_TRACE_PTR,
  RS_DEBUG_TRACE_TILES, RS_DEBUG_TRACE_PASS, RS_DEBUG_LB_SMALL) = range(7)
@@ -87,6 +88,8 @@ _SIGS = {
                                 _i),
     "rs_segmented_workspace_bytes": ([_sz, _sz, _i, _i, _vp], _i),
     "rs_sample_workspace_bytes": ([_sz, _i, _i, _vp], _i),
+    "rs_merge_workspace_bytes": ([_i, _i, _sz, _vp], _i),
+    "rs_merge_sort": ([_i, _i, _vp, _vp, _vp, _vp, _sz, _vp, _sz, _vp, _vp], _i),
     "rs_sample_partition_pairs_u32": ([_vp, _vp, _vp, _vp, _sz, _i, _i, _vp, _vp, _vp, _sz, _vp],
                                       _i),
     "rs_sample_sort_pairs_u32": ([_vp, _vp, _vp, _vp, _sz, _i, _i, _vp, _vp, _sz, _vp, _vp], _i),
@@ -289,6 +292,19 @@ def rs_sample_sort_pairs_u32(keys, vals, keys_out, vals_out, n, samples, buckets
     r = _out_int()
     st = load().rs_sample_sort_pairs_u32(keys, vals, keys_out, vals_out, n, samples, buckets,
                                          d_bucket_offsets, ws, ws_bytes, stream, ctypes.byref(r))
+    return st, r.value
+
+
+def rs_merge_workspace_bytes(key_bytes, val_bytes, n):
+    out = ctypes.c_size_t()
+    st = load().rs_merge_workspace_bytes(key_bytes, val_bytes, n, ctypes.byref(out))
+    return st, out.value
+
+
+def rs_merge_sort(key_bytes, val_bytes, keys, vals, keys_alt, vals_alt, n, ws, ws_bytes, stream):
+    r = _out_int()
+    st = load().rs_merge_sort(key_bytes, val_bytes, keys, vals, keys_alt, vals_alt, n, ws,
+                              ws_bytes, stream, ctypes.byref(r))
     return st, r.value
 
 

@@ -37,7 +37,8 @@ struct Ctrl {
   uint32_t hist_ticket; // upsweep CTAs that have finished
   uint32_t exec_mask;   // bit p: pass p moves the data (written by the upsweep's last CTA)
   uint32_t tile_counter[kMaxPasses];  // dynamic tile ids of each pass
-  uint32_t reserved[64 - 4 - kMaxPasses];
+  uint32_t grid_bar;    // arrivals at the grid barriers of a one-launch sort
+  uint32_t reserved[64 - 5 - kMaxPasses];
 };
 static_assert(sizeof(Ctrl) == 256, "Ctrl must be 256 bytes");
 

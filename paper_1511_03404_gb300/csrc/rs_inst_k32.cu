@@ -15,6 +15,8 @@ const Variant* variants_k32(int* count) {
       SmallSort<uint32_t, 0, 8, 256, 16>::describe(),
       OnesweepSort<uint32_t, 0, 8, 256, 16, 4, true>::describe(),
       OnesweepSort<uint32_t, 0, 8, 256, 16, 5>::describe(),
+      FusedSort<uint32_t, 0, 8, 256, 16, 4>::describe(),
+      FusedSort<uint32_t, 0, 8, 256, 8, 4>::describe(),
   };
   *count = int(sizeof(table) / sizeof(table[0]));
   return table;

@@ -12,6 +12,7 @@ const Variant* variants_k64(int* count) {
       OnesweepSort<uint64_t, 0, 8, 256, 8, 4>::describe(),
       SmallSort<uint64_t, 0, 8, 256, 16>::describe(),
       OnesweepSort<uint64_t, 0, 8, 256, 12, 3, true>::describe(),
+      FusedSort<uint64_t, 0, 8, 256, 12, 3>::describe(),
   };
   *count = int(sizeof(table) / sizeof(table[0]));
   return table;

@@ -14,6 +14,8 @@ const Variant* variants_kv32(int* count) {
       OnesweepSort<uint32_t, 4, 7, 256, 16, 4>::describe(),
       SmallSort<uint32_t, 4, 8, 256, 16>::describe(),
       OnesweepSort<uint32_t, 4, 8, 256, 16, 4, true>::describe(),
+      FusedSort<uint32_t, 4, 8, 256, 16, 4>::describe(),
+      FusedSort<uint32_t, 4, 8, 256, 8, 4>::describe(),
   };
   *count = int(sizeof(table) / sizeof(table[0]));
   return table;

@@ -134,6 +134,35 @@ __device__ __forceinline__ void report_error(Ctrl* ctrl, uint32_t code, uint32_t
   if (atomicCAS(&ctrl->error, 0u, code) == 0u) atomicExch(&ctrl->error_info, info);
 }
 
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Bounded wait until *p >= target.  False when it ran out or another CTA
+// already reported an error.
+__device__ __noinline__ static bool wait_geq(const uint32_t* p, uint32_t target, Ctrl* ctrl,
+                                             uint64_t timeout_ns, uint32_t info) {
+  if (ld_acquire(p) >= target) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 1;; ++it) {
+    if (ld_acquire(p) >= target) return true;
+    if ((it & 63u) == 0u) {
+      if (ld_relaxed(&ctrl->error) != 0u) return false;
+      if (global_ns() - t0 > timeout_ns) {
+        report_error(ctrl, kDevTimeout, info);
+        return false;
+      }
+    }
+  }
+}
+
+
 __device__ __forceinline__ uint32_t warp_inclusive_scan(uint32_t x, int lane) {
 #pragma unroll
   for (int off = 1; off < 32; off <<= 1) {

@@ -6,6 +6,7 @@
 
 #include <algorithm>
 
+#include "rs_fused.cuh"
 #include "rs_host.h"
 #include "rs_kernels.cuh"
 
@@ -115,6 +116,71 @@ struct OnesweepSort {
     v.workspace = &workspace;
     v.run = &run;
     v.count = &count;
+    return v;
+  }
+};
+
+// The whole sort in one cooperative launch (k_fused): for moderate sizes,
+// where the launches of the multi-kernel form dominate.
+template <class K, int VB, int R, int THREADS, int ITEMS, int MINB>
+struct FusedSort {
+  using Base = OnesweepSort<K, VB, R, THREADS, ITEMS, MINB>;
+  using F = FusedSmem<K, VB, R, THREADS, ITEMS>;
+  static constexpr int RADIX = 1 << R;
+
+  static cudaError_t run(const SortArgs& a, int* in_alt) {
+    const int passes = num_passes(a.begin_bit, a.end_bit, R);
+    *in_alt = passes & 1;
+    const size_t nt = Base::tiles(a.n);
+    const Layout L = onesweep_layout(passes, R, nt);
+    char* ws = static_cast<char*>(a.ws);
+    Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws);
+    cudaError_t e = cudaMemsetAsync(ws, 0, L.memset_bytes, a.stream);
+    if (e != cudaSuccess) return e;
+    using V = ValT<VB>;
+    auto kern = &k_fused<K, VB, R, THREADS, ITEMS, MINB>;
+    const int occ = prepare_kernel(reinterpret_cast<const void*>(kern), THREADS, F::BYTES);
+    if (occ <= 0) return cudaErrorInvalidConfiguration;
+    const unsigned grid =
+        unsigned(std::max<size_t>(1, std::min<size_t>(nt, size_t(device_info().sms) * occ)));
+    K* k0 = static_cast<K*>(a.keys);
+    K* k1 = static_cast<K*>(a.keys_alt);
+    V* v0 = static_cast<V*>(a.vals);
+    V* v1 = static_cast<V*>(a.vals_alt);
+    uint32_t n = a.n;
+    int begin = a.begin_bit, end = a.end_bit, np = passes;
+    uint32_t* counts = reinterpret_cast<uint32_t*>(ws + L.counts);
+    uint32_t* status = reinterpret_cast<uint32_t*>(ws + L.status);
+    uint32_t* gagg = reinterpret_cast<uint32_t*>(ws + L.gagg);
+    uint32_t* ginc = reinterpret_cast<uint32_t*>(ws + L.ginc);
+    uint32_t tiles = uint32_t(nt), tiles_pad = uint32_t(L.tiles), groups_pad = uint32_t(L.groups);
+    uint4* zero_base = reinterpret_cast<uint4*>(ws + L.status);
+    uint64_t zero_vec4 = L.status_bytes / 16;
+    Knobs knobs = a.knobs;
+    KeyXf<K> xf = make_key_xf<K>(a.key_kind, a.descending);
+    void* args[] = {&k0, &k1, &v0, &v1, &n, &begin, &end, &np, &counts, &status, &gagg, &ginc,
+                    &tiles, &tiles_pad, &groups_pad, &zero_base, &zero_vec4, &ctrl, &knobs, &xf};
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(THREADS);
+    cfg.dynamicSmemBytes = F::BYTES;
+    cfg.stream = a.stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;  // every CTA resident: the barriers need it
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    prof_before(a.stream);
+    e = cudaLaunchKernelExC(&cfg, reinterpret_cast<const void*>(kern), args);
+    prof_after(a.stream, 1, double(a.n) * (sizeof(K) + passes * 2.0 * (sizeof(K) + VB)));
+    return e;
+  }
+
+  static Variant describe() {
+    Variant v = Base::describe();
+    v.kind = kFused;
+    v.max_n = 1u << 24;
+    v.run = &run;
     return v;
   }
 };

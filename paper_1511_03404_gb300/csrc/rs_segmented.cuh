@@ -72,34 +72,6 @@ inline SegLayout seg_layout(size_t n, size_t nseg, int passes, int radix_bits, i
   return L;
 }
 
-__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
-  uint32_t v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// Bounded wait until *p >= target.  False when it ran out or another CTA
-// already reported an error.
-__device__ __noinline__ static bool wait_geq(const uint32_t* p, uint32_t target, Ctrl* ctrl,
-                                             uint64_t timeout_ns, uint32_t info) {
-  if (ld_acquire(p) >= target) return true;
-  const uint64_t t0 = global_ns();
-  for (uint32_t it = 1;; ++it) {
-    if (ld_acquire(p) >= target) return true;
-    if ((it & 63u) == 0u) {
-      if (ld_relaxed(&ctrl->error) != 0u) return false;
-      if (global_ns() - t0 > timeout_ns) {
-        report_error(ctrl, kDevTimeout, info);
-        return false;
-      }
-    }
-  }
-}
-
 // One CTA numbers the work.  Segments longer than small_max are "long".
 template <int THREADS>
 __global__ void __launch_bounds__(THREADS, 1)

@@ -67,7 +67,7 @@ def test_resident_cta_variants_many_tiles_per_cta(dtype, pairs):
     kb = np.dtype(dtype).itemsize
     vb = kb if pairs else 0
     for var in variants(kb, vb):
-        if var["kind"] != 2:
+        if var["kind"] not in (2, 3):  # resident CTAs; one cooperative launch
             continue
         tile = var["threads"] * var["items"]
         for n in (152 * 4 * tile * 3 + 12345, 152 * 4 * tile * 5):

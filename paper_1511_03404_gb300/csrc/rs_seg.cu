@@ -36,6 +36,11 @@ struct SegSort {
         L.tiles_max, L.chunks_max);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    // short segments: one CTA each, before the persistent kernel
+    auto small = &k_seg_small<K, VB, R, THREADS, ITEMS>;
+    using SS = typename C::SS;
+    const int occ_small = prepare_kernel(reinterpret_cast<const void*>(small), THREADS, SS::BYTES);
+    if (occ_small <= 0) return cudaErrorInvalidConfiguration;
     auto kern = &k_seg_persistent<K, VB, R, THREADS, ITEMS, CHUNK_TILES>;
     const int occ = prepare_kernel(reinterpret_cast<const void*>(kern), THREADS, C::BYTES);
     if (occ <= 0) return cudaErrorInvalidConfiguration;
@@ -57,7 +62,12 @@ struct SegSort {
     a.knobs = knobs;
     using V = ValT<VB>;
     const unsigned grid = unsigned(device_info().sms * occ);
+    const unsigned grid_small =
+        unsigned(std::max<size_t>(1, std::min<size_t>(nseg, size_t(device_info().sms) * occ_small)));
     prof_before(s);
+    small<<<grid_small, THREADS, SS::BYTES, s>>>(static_cast<K*>(keys), static_cast<V*>(vals),
+                                                 static_cast<K*>(keys_alt),
+                                                 static_cast<V*>(vals_alt), a);
     kern<<<grid, THREADS, C::BYTES, s>>>(static_cast<K*>(keys), static_cast<V*>(vals),
                                          static_cast<K*>(keys_alt), static_cast<V*>(vals_alt), a);
     e = cudaGetLastError();

@@ -5,11 +5,14 @@
 //   k_seg_plan        one CTA: classifies segments (short ones fit one CTA,
 //                     long ones are tiled), numbers the work items and maps
 //                     every histogram chunk and pass tile to its segment.
+//   k_seg_small       short segments, each sorted whole in one CTA's shared
+//                     memory (every pass), grid-stride over the short list;
 //   k_seg_persistent  SMs x resident CTAs, each looping over one global work
 //                     queue (an atomic counter) in this order:
 //                       [histogram chunks of long segments]
-//                       [short segments: whole segment sorted in shared memory]
 //                       [pass 0 tiles of long segments] ... [pass P-1 tiles]
+//                     (kept apart from the short segments so that it needs
+//                     few registers and four CTAs fit on an SM)
 //                     A tile of pass p waits (bounded) until its segment's
 //                     histograms are scanned and, for p > 0, until every tile
 //                     of pass p-1 of its segment is written.  Every wait is on
@@ -163,10 +166,12 @@ struct SegKernelCfg {
   static constexpr int TILE = THREADS * ITEMS;
   static constexpr int CHUNK = TILE * CHUNK_TILES;
   static constexpr int MAXP = (8 * int(sizeof(K)) + RADIX_BITS - 1) / RADIX_BITS;
-  static constexpr int HIST_BYTES = MAXP * (RADIX / 2) * 32 * 4;
+  // histogram counters: [pass][digit pair][16 slots], two 16-bit counts per word
+  static constexpr int HIST_SLOTS = 16;
+  static constexpr int HIST_BYTES = MAXP * (RADIX / 2) * HIST_SLOTS * 4;
   using OS = OnesweepSmem<K, VB, RADIX_BITS, THREADS, ITEMS>;
   using SS = SmallSmem<K, VB, RADIX_BITS, THREADS, ITEMS>;
-  static constexpr int A = OS::BYTES > SS::BYTES ? OS::BYTES : SS::BYTES;
+  static constexpr int A = OS::BYTES;
   static constexpr int BODY = A > HIST_BYTES ? A : HIST_BYTES;
   static constexpr int MISC = (BODY + 15) / 16 * 16;  // u32 [8]
   static constexpr int BYTES = MISC + 32;
@@ -188,8 +193,27 @@ struct SegArgs {
   Knobs knobs;
 };
 
+template <class K, int VB, int RADIX_BITS, int THREADS, int ITEMS>
+__global__ void __launch_bounds__(THREADS, 1)
+    k_seg_small(K* __restrict__ k0, ValT<VB>* __restrict__ v0, K* __restrict__ k1,
+                ValT<VB>* __restrict__ v1, SegArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int passes = a.passes;
+  K* kout = (passes & 1) ? k1 : k0;  // where the pass count parity puts the result
+  ValT<VB>* vout = (passes & 1) ? v1 : v0;
+  const uint32_t n_small = a.ctrl->tile_counter[kNSmall];
+  for (uint32_t i = blockIdx.x; i < n_small; i += gridDim.x) {
+    const uint32_t s = a.small_ids[i];
+    const uint64_t b = a.off[s];
+    const uint32_t len = uint32_t(a.off[s + 1] - b);
+    cta_sort<K, VB, RADIX_BITS, THREADS, ITEMS>(k0 + b, v0 + b, kout + b, vout + b, len,
+                                                a.begin_bit, a.end_bit, smem, KeyXf<K>{});
+    __syncthreads();
+  }
+}
+
 template <class K, int VB, int RADIX_BITS, int THREADS, int ITEMS, int CHUNK_TILES>
-__global__ void __launch_bounds__(THREADS, 2)
+__global__ void __launch_bounds__(THREADS, 4)
     k_seg_persistent(K* __restrict__ k0, ValT<VB>* __restrict__ v0, K* __restrict__ k1,
                      ValT<VB>* __restrict__ v1, SegArgs a) {
   using V = ValT<VB>;
@@ -200,15 +224,10 @@ __global__ void __launch_bounds__(THREADS, 2)
   const int tid = threadIdx.x, lane = tid & 31;
   Ctrl* ctrl = a.ctrl;
   const int passes = a.passes;
-  // the sorted data of every segment ends where the pass count parity puts it
-  K* kout = (passes & 1) ? k1 : k0;
-  V* vout = (passes & 1) ? v1 : v0;
 
-  const uint32_t n_small = ctrl->tile_counter[kNSmall];
   const uint32_t n_tiles = ctrl->tile_counter[kNTiles];
   const uint32_t n_chunks = ctrl->tile_counter[kNChunks];
-  const uint32_t q_small = n_chunks;
-  const uint32_t q_pass = n_chunks + n_small;
+  const uint32_t q_pass = n_chunks;
   const uint32_t q_end = q_pass + uint32_t(passes) * n_tiles;
 
   for (;;) {
@@ -220,7 +239,7 @@ __global__ void __launch_bounds__(THREADS, 2)
     const uint32_t item = s_misc[0];
     if (item >= q_end || s_misc[1] != 0u) break;  // CTA-uniform
 
-    if (item < q_small) {
+    if (item < q_pass) {
       // ---- digit histograms of one chunk of a long segment, every pass
       const uint32_t li = a.chunk_seg[item];
       const SegDesc d = a.descs[li];
@@ -229,7 +248,9 @@ __global__ void __launch_bounds__(THREADS, 2)
       const uint32_t len = min(uint32_t(CHUNK), d.len - start);
       const K* keys = k0 + d.off + start;
       uint32_t* sh = reinterpret_cast<uint32_t*>(smem);
-      for (int i = tid; i < passes * HALF * 32; i += THREADS) sh[i] = 0u;
+      constexpr int SL = C::HIST_SLOTS;
+      const int slot = lane & (SL - 1);
+      for (int i = tid; i < passes * HALF * SL; i += THREADS) sh[i] = 0u;
       __syncthreads();
       for (uint32_t i = tid; i < len; i += THREADS) {
         const K k = keys[i];
@@ -237,16 +258,16 @@ __global__ void __launch_bounds__(THREADS, 2)
           const int lo = a.begin_bit + p * RADIX_BITS;
           const uint32_t m = (1u << (min(lo + RADIX_BITS, a.end_bit) - lo)) - 1u;
           const uint32_t dg = digit_of(k, uint32_t(lo), m);
-          atomicAdd(&sh[(p * HALF + int(dg >> 1)) * 32 + lane], 1u << ((dg & 1u) << 4));
+          atomicAdd(&sh[(p * HALF + int(dg >> 1)) * SL + slot], 1u << ((dg & 1u) << 4));
         }
       }
       __syncthreads();
       uint32_t* cnt = a.counts + size_t(li) * passes * RADIX;
       for (int w = tid; w < passes * HALF; w += THREADS) {
         uint32_t lo = 0u, hi = 0u;
-        const uint32_t* row = sh + w * 32;
-        for (int l = 0; l < 32; ++l) {
-          const uint32_t x = row[(l + lane) & 31];
+        const uint32_t* row = sh + w * SL;
+        for (int l = 0; l < SL; ++l) {
+          const uint32_t x = row[(l + slot) & (SL - 1)];
           lo += x & 0xFFFFu;
           hi += x >> 16;
         }
@@ -292,13 +313,6 @@ __global__ void __launch_bounds__(THREADS, 2)
           st_release(&state[kSegReady], 1u);
         }
       }
-    } else if (item < q_pass) {
-      // ---- one short segment, every pass in shared memory
-      const uint32_t s = a.small_ids[item - q_small];
-      const uint64_t b = a.off[s];
-      const uint32_t len = uint32_t(a.off[s + 1] - b);
-      cta_sort<K, VB, RADIX_BITS, THREADS, ITEMS>(k0 + b, v0 + b, kout + b, vout + b, len,
-                                                  a.begin_bit, a.end_bit, smem, KeyXf<K>{});
     } else {
       // ---- one tile of one pass of a long segment
       const uint32_t q = item - q_pass;

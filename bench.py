@@ -332,7 +332,8 @@ def run_ours(args):
                         for i, d in enumerate(dists) if step_ms[i::len(dists)]},
         "cpu_baseline": None,
         "e2e": {"value": e2e["value"], "unit": "Gkeys/s",
-                "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]},
+                "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
+                "serial": e2e.get("serial"), "pipelining": e2e.get("pipelining")},
         "gpu_launches": launches,
         "clocks": clocks.summary(),
         "kernel_source": src,
@@ -383,39 +384,67 @@ def check_sorted(torch, k_out, v_out, k_in) -> bool:
 
 
 def e2e_rate(torch, rs, keys_h, vals_h, n, dev, ws, args, dists) -> dict:
-    """Host -> device copy, sort, device -> host copy, per step, through the C ABI."""
+    """Host -> device copy, sort, device -> host copy, per step, through the C ABI.
+
+    Two steps are in flight on two streams (two sets of device buffers and
+    workspaces, two sets of pinned host outputs), so that one step's copies
+    run while the other sorts; ``serial`` is the same with one stream."""
     hk = {d: torch.from_numpy(keys_h[d].view(np.int32)).pin_memory() for d in dists}
     hv = torch.from_numpy(vals_h.view(np.int32)).pin_memory()
-    ok = torch.empty(n, dtype=torch.int32).pin_memory()
-    ov = torch.empty(n, dtype=torch.int32).pin_memory()
-    k = torch.empty(n, dtype=torch.int32, device=dev)
-    v, ka, va = torch.empty_like(k), torch.empty_like(k), torch.empty_like(k)
-    stream = torch.cuda.current_stream(dev)
-    h = stream.cuda_stream
+    slots = []
+    for j in range(2):
+        k = torch.empty(n, dtype=torch.int32, device=dev)
+        slots.append({
+            "stream": torch.cuda.Stream(dev),
+            "k": k, "v": torch.empty_like(k), "ka": torch.empty_like(k), "va": torch.empty_like(k),
+            "ok": torch.empty(n, dtype=torch.int32).pin_memory(),
+            "ov": torch.empty(n, dtype=torch.int32).pin_memory(),
+            "ws": ws if j == 0 else torch.empty_like(ws),
+        })
 
-    def step(i):
+    def step(i, sl):
         d = dists[i % len(dists)]
-        k.copy_(hk[d], non_blocking=True)
-        v.copy_(hv, non_blocking=True)
-        st, in_alt = rs.rs_sort_pairs_u32(k.data_ptr(), v.data_ptr(), ka.data_ptr(),
-                                          va.data_ptr(), n, 0, 32, ws.data_ptr(), ws.numel(), h)
-        rs.check(st, "rs_sort_pairs_u32")
-        ok.copy_(ka if in_alt else k, non_blocking=True)
-        ov.copy_(va if in_alt else v, non_blocking=True)
+        with torch.cuda.stream(sl["stream"]):
+            h = sl["stream"].cuda_stream
+            sl["k"].copy_(hk[d], non_blocking=True)
+            sl["v"].copy_(hv, non_blocking=True)
+            st, in_alt = rs.rs_sort_pairs_u32(sl["k"].data_ptr(), sl["v"].data_ptr(),
+                                              sl["ka"].data_ptr(), sl["va"].data_ptr(), n, 0, 32,
+                                              sl["ws"].data_ptr(), sl["ws"].numel(), h)
+            rs.check(st, "rs_sort_pairs_u32")
+            sl["ok"].copy_(sl["ka"] if in_alt else sl["k"], non_blocking=True)
+            sl["ov"].copy_(sl["va"] if in_alt else sl["v"], non_blocking=True)
 
-    steps = max(3, min(args.steps, 12))
-    for i in range(3):
-        step(i)
-    torch.cuda.synchronize()
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
-    t0.record(stream)
-    for i in range(steps):
-        step(i)
-    t1.record(stream)
-    torch.cuda.synchronize()
-    ms = t0.elapsed_time(t1) / steps
-    return {"value": n / (ms / 1e3) / 1e9, "ms_per_step": ms, "h2d": 2 * 4 * n, "d2h": 2 * 4 * n}
+    def timed(nslots):
+        steps = max(4, min(args.steps, 12))
+        for i in range(3):
+            step(i, slots[i % nslots])
+        torch.cuda.synchronize()
+        s0 = slots[0]["stream"]
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(s0)
+        for j in range(1, nslots):  # every stream starts after t0
+            slots[j]["stream"].wait_event(t0)
+        for i in range(steps):
+            step(i, slots[i % nslots])
+        for j in range(1, nslots):  # and t1 follows every stream's last step
+            e = torch.cuda.Event()
+            e.record(slots[j]["stream"])
+            s0.wait_event(e)
+        t1.record(s0)
+        torch.cuda.synchronize()
+        return t0.elapsed_time(t1) / steps
+
+    ms_serial = timed(1)
+    ms = timed(2)
+    # the last outputs are complete and sorted
+    for sl in slots:
+        assert np.all(np.diff(sl["ok"].numpy().view(np.uint32)) >= 0)
+    return {"value": n / (ms / 1e3) / 1e9, "ms_per_step": ms, "h2d": 2 * 4 * n, "d2h": 2 * 4 * n,
+            "serial": {"value": n / (ms_serial / 1e3) / 1e9, "ms_per_step": ms_serial},
+            "pipelining": "two steps in flight on two streams (copies of one overlap the other's "
+                          "sort); serial: one stream"}
 
 
 def _time_sorts(torch, rs, kb, vb, keys, vals, reps, stream):

@@ -122,8 +122,9 @@ int rs_num_variants(int key_bytes, int val_bytes);
  * per CTA, keys per thread, and kind (0 = multi-CTA onesweep with one CTA per
  * tile, 1 = one CTA sorting the whole array in shared memory, 2 = onesweep on
  * resident CTAs that each take tile after tile, 3 = the whole sort in one
- * cooperative launch with grid barriers between the passes); max_n bounds
- * the array size.
+ * cooperative launch with grid barriers between the passes, 4 = one
+ * thread-block cluster sorting the whole array in its distributed shared
+ * memory); max_n bounds the array size.
  */
 rs_status rs_variant_info(int key_bytes, int val_bytes, int index, int* radix_bits,
                           int* threads, int* items_per_thread, int* kind, size_t* max_n);

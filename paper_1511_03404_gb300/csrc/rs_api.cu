@@ -338,7 +338,7 @@ rs_status rs_digit_counts(int key_bytes, const void* keys, size_t n, int begin_b
   const Variant* all = variants(key_bytes, 0, &count);
   const Variant* v = nullptr;
   for (int i = 0; i < count && !v; ++i)
-    if (all[i].kind != kSmall && all[i].radix_bits == radix_bits) v = &all[i];
+    if (all[i].count != nullptr && all[i].radix_bits == radix_bits) v = &all[i];
   if (!v) return RS_ERR_INVALID;
   const int passes = num_passes(begin_bit, end_bit, radix_bits);
   const Layout L = onesweep_layout(passes, radix_bits, 0);

@@ -27,7 +27,7 @@ struct SortArgs {
   int descending = 0;
 };
 
-enum VariantKind { kOnesweep = 0, kSmall = 1, kOnesweepPersist = 2, kFused = 3 };
+enum VariantKind { kOnesweep = 0, kSmall = 1, kOnesweepPersist = 2, kFused = 3, kCluster = 4 };
 
 struct Variant {
   int key_bytes, val_bytes;

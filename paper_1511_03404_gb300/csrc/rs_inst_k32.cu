@@ -17,6 +17,7 @@ const Variant* variants_k32(int* count) {
       OnesweepSort<uint32_t, 0, 8, 256, 16, 5>::describe(),
       FusedSort<uint32_t, 0, 8, 256, 16, 4>::describe(),
       FusedSort<uint32_t, 0, 8, 256, 8, 4>::describe(),
+      ClusterSort<uint32_t, 0, 8, 512, 16, 8>::describe(),
   };
   *count = int(sizeof(table) / sizeof(table[0]));
   return table;

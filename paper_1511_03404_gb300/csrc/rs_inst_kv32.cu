@@ -16,6 +16,7 @@ const Variant* variants_kv32(int* count) {
       OnesweepSort<uint32_t, 4, 8, 256, 16, 4, true>::describe(),
       FusedSort<uint32_t, 4, 8, 256, 16, 4>::describe(),
       FusedSort<uint32_t, 4, 8, 256, 8, 4>::describe(),
+      ClusterSort<uint32_t, 4, 8, 512, 16, 8>::describe(),
   };
   *count = int(sizeof(table) / sizeof(table[0]));
   return table;

@@ -6,6 +6,7 @@
 
 #include <algorithm>
 
+#include "rs_cluster.cuh"
 #include "rs_fused.cuh"
 #include "rs_host.h"
 #include "rs_kernels.cuh"
@@ -181,6 +182,66 @@ struct FusedSort {
     v.kind = kFused;
     v.max_n = 1u << 24;
     v.run = &run;
+    return v;
+  }
+};
+
+// The whole sort in one thread-block cluster of up to CL CTAs
+// (k_cluster_sort): arrays of up to CL x THREADS x ITEMS elements stay in
+// the cluster's shared memory for every pass.
+template <class K, int VB, int R, int THREADS, int ITEMS, int CL>
+struct ClusterSort {
+  using S = ClusterSmem<K, VB, R, THREADS, ITEMS>;
+  static_assert(CL >= 1 && CL <= S::MAX_CL, "portable cluster sizes");
+
+  static size_t workspace(uint32_t, int) { return 0; }
+
+  static cudaError_t run(const SortArgs& a, int* in_alt) {
+    using V = ValT<VB>;
+    *in_alt = 0;  // sorted in place
+    auto kern = &k_cluster_sort<K, VB, R, THREADS, ITEMS>;
+    if (prepare_kernel(reinterpret_cast<const void*>(kern), THREADS, S::BYTES) <= 0)
+      return cudaErrorInvalidConfiguration;
+    const unsigned ncta = unsigned((size_t(a.n) + S::SLICE - 1) / S::SLICE);
+    if (ncta < 1 || ncta > unsigned(CL)) return cudaErrorInvalidValue;
+    Ctrl* ctrl = (a.ws != nullptr && a.ws_bytes >= sizeof(Ctrl)) ? static_cast<Ctrl*>(a.ws)
+                                                                  : nullptr;
+    K* keys = static_cast<K*>(a.keys);
+    V* vals = static_cast<V*>(a.vals);
+    uint32_t n = a.n;
+    int begin = a.begin_bit, end = a.end_bit;
+    KeyXf<K> xf = make_key_xf<K>(a.key_kind, a.descending);
+    void* args[] = {&keys, &vals, &n, &begin, &end, &ctrl, &xf};
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ncta);
+    cfg.blockDim = dim3(THREADS);
+    cfg.dynamicSmemBytes = S::BYTES;
+    cfg.stream = a.stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;  // the whole grid is one cluster
+    attr[0].val.clusterDim.x = ncta;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    prof_before(a.stream);
+    const cudaError_t e = cudaLaunchKernelExC(&cfg, reinterpret_cast<const void*>(kern), args);
+    prof_after(a.stream, 2, 2.0 * double(a.n) * double(sizeof(K) + VB));
+    return e;
+  }
+
+  static Variant describe() {
+    Variant v{};
+    v.key_bytes = int(sizeof(K));
+    v.val_bytes = VB;
+    v.kind = kCluster;
+    v.radix_bits = R;
+    v.threads = THREADS;
+    v.items = ITEMS;
+    v.max_n = uint32_t(CL) * uint32_t(S::SLICE);
+    v.workspace = &workspace;
+    v.run = &run;
+    v.count = nullptr;
     return v;
   }
 };

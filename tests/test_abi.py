@@ -53,7 +53,7 @@ def test_variants_described():
             info = rs.rs_variant_info(kb, vb, i)
             assert 4 <= info["radix_bits"] <= 8 and info["threads"] % 32 == 0
             kinds.add(info["kind"])
-        assert {0, 1} <= kinds <= {0, 1, 2, 3}
+        assert {0, 1} <= kinds <= {0, 1, 2, 3, 4}
     assert rs.rs_num_variants(4, 8) == 0
     with pytest.raises(rs.RsError):
         rs.rs_variant_info(4, 4, 99)

@@ -55,6 +55,8 @@ def test_every_variant_tile_boundaries(dtype, pairs):
     for var in variants(kb, vb):
         tile = var["threads"] * var["items"]
         sizes = {2, 3, 31, 32, 33, tile - 1, tile, tile + 1, 2 * tile + 7, 5 * tile}
+        if var["max_n"] <= 1 << 17:  # one-CTA and one-cluster kinds: their largest arrays
+            sizes |= {var["max_n"] - 1, var["max_n"]}
         for n in sorted(s for s in sizes if s <= var["max_n"]):
             for dist in ("uniform", "entropy16", "zero", "sorted_desc"):
                 check_case(dtype, pairs, dist, n, variant=var["index"])

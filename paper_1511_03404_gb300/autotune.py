@@ -81,7 +81,11 @@ def tune(sizes=SIZES, types=TYPES, reps=5, log=print, verbose=False) -> dict:
                     continue
                 if verbose:
                     print(f"  k{kb} v{vb} n={n} variant {i}", file=sys.stderr, flush=True)
-                ms = _time_variant(torch, kb, vb, n, i, keys, vals, reps)
+                try:
+                    ms = _time_variant(torch, kb, vb, n, i, keys, vals, reps)
+                except rs.RsError as err:  # a form this GPU cannot launch: leave it out
+                    log(f"k{kb} v{vb} n={n} variant {i}: skipped ({err})")
+                    continue
                 if ms is not None:
                     results[i] = ms
             best = min(results, key=results.get)

@@ -88,6 +88,8 @@ struct Request {
 
 struct Unit;  // one admitted sort or batch
 
+constexpr size_t kMaxBatchMembers = 1024;
+
 }  // namespace
 
 struct rs_server {
@@ -99,6 +101,13 @@ struct rs_server {
   std::vector<int> stream_busy;
   size_t batch_max_n = 1u << 14;  // requests up to this size share a segmented launch
   size_t max_batch_keys = 1u << 22;
+  // Large requests (at least large_n keys) are admitted at most max_large at a
+  // time, oldest first: running many at once only splits the copy bandwidth
+  // between them and stretches every one (the tail of the latency), while
+  // shorter requests keep the other streams.
+  size_t large_n = size_t(1) << 21;
+  int max_large = 2;
+  int large_running = 0;
   std::mutex mu;
   std::condition_variable cv;
   std::deque<uint64_t> pending;
@@ -106,6 +115,9 @@ struct rs_server {
   std::vector<Unit*> finished;  // completed units, handed over by the host callbacks
   uint64_t changes = 0;         // bumped by every submit, cancel and completion
   uint32_t* status_slab = nullptr;  // pinned, one device-status word per stream
+  // pinned, per stream: the segment offsets of a batch (a copy from pageable
+  // memory would wait for the stream's earlier copies and stall the scheduler)
+  uint64_t* off_slab = nullptr;
   uint64_t next_id = 1;
   bool stop = false;
   std::thread sched;
@@ -123,6 +135,7 @@ struct Unit {
   std::vector<std::shared_ptr<Request>> members;
   size_t pool_off = 0, pool_bytes = 0;
   int stream = 0;
+  bool large = false;
   uint32_t* h_status = nullptr;  // pinned: device status word of the sort
 };
 
@@ -236,7 +249,8 @@ rs_status launch_batch(rs_server* s, Unit* u, const BatchPlan& b) {
   cudaStream_t st = s->streams[u->stream];
   char* base = s->pool_base + u->pool_off;
   const size_t nseg = u->members.size();
-  std::vector<uint64_t> off(nseg + 1, 0);
+  uint64_t* off = s->off_slab + size_t(u->stream) * (kMaxBatchMembers + 1);
+  off[0] = 0;
   for (size_t i = 0; i < nseg; ++i) off[i + 1] = off[i] + u->members[i]->req.n;
   // every member in a batch has the same bit range (the scheduler groups them)
   const int begin_bit = u->members[0]->req.begin_bit, end_bit = u->members[0]->req.end_bit;
@@ -246,8 +260,7 @@ rs_status launch_batch(rs_server* s, Unit* u, const BatchPlan& b) {
         cudaMemcpyAsync(base + b.v + off[i] * 4, q.h_vals, q.n * 4, cudaMemcpyHostToDevice, st))
       return RS_ERR_CUDA;
   }
-  // pageable source: the call returns once the offsets are staged
-  if (cudaMemcpyAsync(base + b.off, off.data(), (nseg + 1) * 8, cudaMemcpyHostToDevice, st))
+  if (cudaMemcpyAsync(base + b.off, off, (nseg + 1) * 8, cudaMemcpyHostToDevice, st))
     return RS_ERR_CUDA;
   int in_alt = 0;
   rs_status rs_st = rs_segmented_sort_pairs(
@@ -280,6 +293,7 @@ void finish_unit(rs_server* s, Unit* u, rs_status st) {
   // caller holds s->mu
   s->pool->release(u->pool_off, u->pool_bytes);
   s->stream_busy[u->stream] = 0;
+  if (u->large) s->large_running -= 1;
   rs_status dev = RS_OK;
   if (st == RS_OK && u->h_status && *u->h_status != 0u)
     dev = (*u->h_status == rs::kDevTimeout) ? RS_ERR_TIMEOUT
@@ -331,6 +345,7 @@ void scheduler(rs_server* s) {
     size_t batch_keys = 0;
     std::vector<uint64_t> keep;  // looked at, still queued, in order
     int looked = 0;
+    bool large_blocked = false;  // large requests are admitted in submission order
     while (!s->pending.empty() && looked < 256) {
       const uint64_t id = s->pending.front();
       s->pending.pop_front();
@@ -341,7 +356,8 @@ void scheduler(rs_server* s) {
       if (batchable(s, r->req)) {
         const bool same_bits = batch.empty() || (batch[0]->req.begin_bit == r->req.begin_bit &&
                                                  batch[0]->req.end_bit == r->req.end_bit);
-        if (same_bits && batch_keys + r->req.n <= s->max_batch_keys) {
+        if (same_bits && batch_keys + r->req.n <= s->max_batch_keys &&
+            batch.size() < kMaxBatchMembers) {
           batch.push_back(r);
           batch_keys += r->req.n;
         } else {
@@ -349,15 +365,24 @@ void scheduler(rs_server* s) {
         }
         continue;
       }
+      const bool large = r->req.n >= s->large_n;
+      if (large && (large_blocked || s->large_running >= s->max_large)) {
+        large_blocked = true;  // later large requests wait behind this one
+        keep.push_back(id);
+        continue;
+      }
       const int si = free_stream(s);
       size_t off = 0;
       const size_t need = single_footprint(r->req);
       if (si < 0 || !s->pool->alloc(need, &off)) {
+        if (large) large_blocked = true;
         keep.push_back(id);
         continue;
       }
       Unit* u = new Unit;
       u->srv = s;
+      u->large = large;
+      if (large) s->large_running += 1;
       u->members.push_back(r);
       u->pool_off = off;
       u->pool_bytes = rs::align_up(std::max<size_t>(need, 256), 256);
@@ -428,6 +453,15 @@ rs_status rs_server_create(size_t budget_bytes, int streams, rs_server** out) {
     delete s;
     return RS_ERR_NOMEM;
   }
+  if (cudaHostAlloc(reinterpret_cast<void**>(&s->off_slab),
+                    sizeof(uint64_t) * (kMaxBatchMembers + 1) * streams,
+                    cudaHostAllocDefault) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFreeHost(s->status_slab);
+    cudaFree(s->pool_base);
+    delete s;
+    return RS_ERR_NOMEM;
+  }
   s->streams.resize(streams);
   s->stream_busy.assign(streams, 0);
   for (auto& st : s->streams) {
@@ -437,6 +471,7 @@ rs_status rs_server_create(size_t budget_bytes, int streams, rs_server** out) {
         if (t) cudaStreamDestroy(t);
       cudaFree(s->pool_base);
       cudaFreeHost(s->status_slab);
+      cudaFreeHost(s->off_slab);
       delete s;
       return RS_ERR_CUDA;
     }
@@ -466,6 +501,7 @@ rs_status rs_server_destroy(rs_server* s) {
   for (auto& st : s->streams) cudaStreamDestroy(st);
   cudaFree(s->pool_base);
   cudaFreeHost(s->status_slab);
+  cudaFreeHost(s->off_slab);
   delete s;
   return RS_OK;
 }

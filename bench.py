@@ -19,7 +19,9 @@ from __future__ import annotations
 
 import argparse
 import faulthandler
+import gc
 import hashlib
+import itertools
 import json
 import os
 import statistics
@@ -339,14 +341,14 @@ def run_ours(args):
         "kernel_source": src,
     }
     if not (args.no_extras or args.quick) and world == 1:
+        stage("serving: Poisson trace")
+        line["serving"] = bench_serving_process(args.serve_seconds)
         stage("u32 keys, 2^20 (launch-bound)")
         line["u32_keys_2p20"] = bench_u32_keys_small(torch, rs, dev)
         stage("u64 keys and pairs, 2^27")
         line["u64_2p27"] = bench_u64(torch, rs, dev)
         stage("segmented: batched vs plain")
         line["segmented"] = bench_segmented(torch, rs, dev, args.seg_scaled)
-        stage("serving: Poisson trace")
-        line["serving"] = bench_serving(torch, rs, seconds=args.serve_seconds)
     if not (args.no_cpu_baseline or args.quick):
         stage("cpu baseline (oracle)")
         line["cpu_baseline"] = cpu_oracle_rate(1 << 24)
@@ -675,7 +677,9 @@ def bench_serving(torch, rs, seconds: float = 10.0, rate: float = 5000.0,
             poll_some(block=True)
 
     def poll_some(block=False):
-        for hnd in list(pending):
+        # the oldest requests first, a bounded number per call, so that the
+        # submission loop keeps to the arrival schedule when many are in flight
+        for hnd in list(itertools.islice(pending, 64)):
             st_, done = rs.rs_poll(srv, hnd)
             if done:
                 if st_ != rs.RS_OK:
@@ -685,6 +689,10 @@ def bench_serving(torch, rs, seconds: float = 10.0, rate: float = 5000.0,
             time.sleep(0.0002)
 
     arrival = np.cumsum(gaps)
+    # no cyclic garbage collection while the client keeps the arrival
+    # schedule: a full collection over a large heap stalls it for tens of ms
+    gc.collect()
+    gc.disable()
     t0 = time.perf_counter()
     for i in range(count):
         while time.perf_counter() - t0 < arrival[i]:
@@ -706,6 +714,7 @@ def bench_serving(torch, rs, seconds: float = 10.0, rate: float = 5000.0,
             reqs = reqs[-4096:]
     while pending:
         poll_some(block=True)
+    gc.enable()
     st, stats = rs.rs_server_stats(srv)
     rs.check(st, "rs_server_stats")
     rs.rs_server_destroy(srv)
@@ -717,6 +726,24 @@ def bench_serving(torch, rs, seconds: float = 10.0, rate: float = 5000.0,
             "batched_requests": stats["batched_requests"], "max_queued": stats["max_queued"],
             "pool_peak_gib": stats["pool_peak_bytes"] / 2**30,
             "latency": "submit -> completion callback, host pinned buffers in and out"}
+
+
+def bench_serving_process(seconds: float) -> dict:
+    """The serving trace in a child process of its own, the way a sort server
+    runs: the benchmark's own process holds tens of GB of device and pinned
+    host buffers by then, which a serving process does not."""
+    code = ("import json, sys; sys.path.insert(0, %r); import torch, bench; "
+            "from paper_1511_03404_gb300 import rs; rs.load(); "
+            "print('SERVING ' + json.dumps(bench.bench_serving(torch, rs, seconds=%r)))"
+            % (ROOT, float(seconds)))
+    res = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True,
+                         timeout=600)
+    for line in res.stdout.splitlines():
+        if line.startswith("SERVING "):
+            out = json.loads(line[len("SERVING "):])
+            out["process"] = "own process (a dedicated serving process)"
+            return out
+    raise SystemExit(f"bench: serving child failed ({res.returncode}): {res.stderr[-2000:]}")
 
 
 def stage(msg: str) -> None:

@@ -121,7 +121,7 @@ def load():
             lib = ctypes.CDLL(path, mode=ctypes.RTLD_GLOBAL)
             for name, (args, res) in _SIGS.items():
                 if not hasattr(lib, name):
-                    continue  # declared later in the header than this build
+                    continue  # a library built from an older header
                 fn = getattr(lib, name)
                 fn.argtypes = args
                 fn.restype = res

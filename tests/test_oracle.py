@@ -251,7 +251,7 @@ def test_segmented(dtype):
 
 def test_stored_oracle_hashes():
     """Hashes written by tests/golden/make_golden.py catch platform drift
-    (the GPU machine is aarch64, this container x86_64)."""
+    (the oracle must give the same bytes on x86_64 and aarch64 hosts)."""
     path = os.path.join(os.path.dirname(__file__), "golden", "oracle_sha256.json")
     with open(path) as f:
         golden = json.load(f)

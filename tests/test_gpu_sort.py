@@ -6,6 +6,8 @@ keys and values element by element with the oracle's result (arXiv
 several tiles and ragged tails, the 2^n + 2^(n-1) lengths of Sec. 3, and the
 degenerate cases (n = 0, 1, one digit value, every pass skipped).
 """
+import time
+
 import numpy as np
 import pytest
 
@@ -198,6 +200,45 @@ def test_argument_errors_on_device_buffers():
                                h)[0] == rs.RS_ERR_INVALID
     assert rs.rs_sort_keys_u32(d.data_ptr(), a.data_ptr(), rs.RS_MAX_N + 1, 0, 32, ws.data_ptr(),
                                need, h)[0] == rs.RS_ERR_INVALID
+
+
+@pytest.mark.parametrize("vb", [0, 4], ids=["k32", "kv32"])
+def test_every_multi_cta_form_gives_up_in_bounded_time(vb):
+    """The same dropped tile under every form that waits on other CTAs (one
+    CTA per tile, resident CTAs taking tile after tile, one cooperative
+    launch with grid barriers): each reports RS_ERR_TIMEOUT in bounded time,
+    and the context sorts correctly afterwards."""
+    n = 2**20
+    k = inputs.keys(np.uint32, "uniform", n)
+    v = inputs.values(np.uint32, n)
+    h = torch.cuda.current_stream().cuda_stream
+    tested = set()
+    for var in variants(4, vb):
+        if var["kind"] not in (0, 2, 3) or var["max_n"] < n:
+            continue
+        tested.add(var["kind"])
+        try:
+            rs.check(rs.rs_debug_set(rs.RS_DEBUG_TIMEOUT_NS, 20_000_000))
+            rs.check(rs.rs_debug_set(rs.RS_DEBUG_DROP_PUBLISH_PASS, 1))
+            rs.check(rs.rs_debug_set(rs.RS_DEBUG_DROP_PUBLISH_TILE, 3))
+            dk, dv = to_dev(k, torch), to_dev(v, torch)
+            ka, va = torch.empty_like(dk), torch.empty_like(dv)
+            st, need = rs.rs_workspace_bytes(4, vb, n, 0, 32, 0, var["index"])
+            ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+            t0 = time.time()
+            rs.check(rs.rs_sort(4, vb, dk.data_ptr(), dv.data_ptr() if vb else None,
+                                ka.data_ptr(), va.data_ptr() if vb else None, n, 0, 32,
+                                ws.data_ptr(), need, h, 0, var["index"])[0])
+            st, info = rs.rs_workspace_status(ws.data_ptr(), h)
+            assert st == rs.RS_ERR_TIMEOUT, (var, st)
+            assert info > 3, (var, info)
+            assert time.time() - t0 < 30, var
+        finally:
+            rs.rs_debug_set(rs.RS_DEBUG_DROP_PUBLISH_TILE, -1)
+            rs.rs_debug_set(rs.RS_DEBUG_DROP_PUBLISH_PASS, -1)
+            rs.rs_debug_set(rs.RS_DEBUG_TIMEOUT_NS, 1_000_000_000)
+        check_case(np.uint32, vb > 0, "uniform", n, variant=var["index"])
+    assert tested == {0, 2, 3}
 
 
 def test_lookback_wait_is_bounded():

@@ -276,10 +276,10 @@ rs_status rs_sample_sort_pairs_u32(uint32_t* keys, uint32_t* vals, uint32_t* key
  *   keys, vals, keys_alt, vals_alt  [n] device arrays (double buffer); the
  *             result ends in keys / vals (*result_in_alt = 0) or in the
  *             alternates (1): the parity of the number of merge passes,
- *             ceil(log2(ceil(n / 2048)))
+ *             ceil(log2(ceil(n / 4096)))
  *   ws        device workspace of rs_merge_workspace_bytes() bytes, 256-byte
  *             aligned (the merge-path split of every output tile)
- * Tiles of 2048 elements are sorted inside one CTA each, then runs are merged
+ * Tiles of 4096 elements are sorted inside one CTA each, then runs are merged
  * pairwise, each CTA producing one tile of the output from the two input
  * ranges a merge-path search delimits.  Equal keys keep their input order.
  * Asynchronous on `stream`.  Bad types, sizes, pointers or alignment:

@@ -1,7 +1,7 @@
 // Merge sort (Sec. 2.4, the parallel merge sort of Satish et al.): a
 // comparison sort, stable, for keys that the radix passes do not take
 // (128-bit keys) as well as 32- and 64-bit keys.
-//   k_ms_tile   sorts each tile of kTile elements in one CTA: a stable
+//   k_ms_tile   sorts each tile of kTile (4096) elements in one CTA: a stable
 //               odd-even transposition sort of each thread's kItems
 //               consecutive elements in registers, then merge rounds of
 //               doubling width in shared memory;
@@ -22,7 +22,7 @@ namespace rs {
 namespace {
 
 constexpr int kMsThreads = 256;
-constexpr int kMsItems = 8;
+constexpr int kMsItems = 16;
 constexpr int kTile = kMsThreads * kMsItems;
 
 // A 128-bit unsigned key: value = lo + 2^64 * hi (little-endian words).
@@ -47,10 +47,23 @@ __device__ __forceinline__ Key128 key_max<Key128>() { return Key128{~0ull, ~0ull
 
 struct NoVal {};
 
+// Shared-memory slot of element i: one pad slot after every 32 elements, so
+// that a warp reading or writing each thread's kMsItems consecutive elements
+// (stride kMsItems) spreads over the banks instead of hitting a few.
+__device__ __forceinline__ uint32_t pad(uint32_t i) { return i + (i >> 5); }
+
+// A run of elements in shared memory, indexed through pad().
+template <class T>
+struct Padded {
+  T* base;
+  uint32_t first;  // element index of run[0]
+  __device__ __forceinline__ T& operator[](uint32_t i) const { return base[pad(first + i)]; }
+};
+
 // Elements taken from the left run a[0 .. na) at diagonal `diag` of the merge
 // of a and b[0 .. nb): the largest i with a[i-1] <= b[diag-i] (ties: a first).
-template <class K>
-__device__ __forceinline__ uint32_t merge_path(const K* a, uint32_t na, const K* b, uint32_t nb,
+template <class A, class B>
+__device__ __forceinline__ uint32_t merge_path(const A& a, uint32_t na, const B& b, uint32_t nb,
                                                uint32_t diag) {
   uint32_t lo = diag > nb ? diag - nb : 0u;
   uint32_t hi = min(diag, na);
@@ -64,9 +77,9 @@ __device__ __forceinline__ uint32_t merge_path(const K* a, uint32_t na, const K*
 
 // Merge min(kMsItems, na - i + nb - j) outputs, starting at (a + i, b + j),
 // into registers.
-template <class K, class V, bool HAS_V>
-__device__ __forceinline__ void merge_items(const K* a, const V* av, uint32_t na, const K* b,
-                                            const V* bv, uint32_t nb, uint32_t i, uint32_t j,
+template <class K, class V, bool HAS_V, class RK, class RV>
+__device__ __forceinline__ void merge_items(const RK& a, const RV& av, uint32_t na, const RK& b,
+                                            const RV& bv, uint32_t nb, uint32_t i, uint32_t j,
                                             K (&k)[kMsItems], V (&v)[kMsItems]) {
 #pragma unroll
   for (int t = 0; t < kMsItems; ++t) {
@@ -86,9 +99,10 @@ __device__ __forceinline__ void merge_items(const K* a, const V* av, uint32_t na
 
 template <class K, class V, bool HAS_V>
 struct MsSmem {
+  static constexpr int SLOTS = kTile + kTile / 32;  // with the pad slots
   static constexpr int KEYS = 0;
-  static constexpr int VALS = (kTile * int(sizeof(K)) + 15) / 16 * 16;
-  static constexpr int BYTES = VALS + (HAS_V ? kTile * int(sizeof(V)) : 0);
+  static constexpr int VALS = (SLOTS * int(sizeof(K)) + 15) / 16 * 16;
+  static constexpr int BYTES = VALS + (HAS_V ? SLOTS * int(sizeof(V)) : 0);
 };
 
 // One tile per CTA, sorted in place (src may equal dst).
@@ -105,8 +119,8 @@ __global__ void __launch_bounds__(kMsThreads) k_ms_tile(const K* src, const V* v
   // past the end: the largest key; being last in input order too, the
   // padding stays behind every real key (stability)
   for (uint32_t i = tid; i < uint32_t(kTile); i += kMsThreads) {
-    sk[i] = i < len ? src[base + i] : key_max<K>();
-    if constexpr (HAS_V) sv[i] = i < len ? vsrc[base + i] : V{};
+    sk[pad(i)] = i < len ? src[base + i] : key_max<K>();
+    if constexpr (HAS_V) sv[pad(i)] = i < len ? vsrc[base + i] : V{};
   }
   __syncthreads();
   K k[kMsItems];
@@ -114,8 +128,8 @@ __global__ void __launch_bounds__(kMsThreads) k_ms_tile(const K* src, const V* v
   const uint32_t o = uint32_t(tid) * kMsItems;
 #pragma unroll
   for (int t = 0; t < kMsItems; ++t) {
-    k[t] = sk[o + t];
-    if constexpr (HAS_V) v[t] = sv[o + t];
+    k[t] = sk[pad(o + t)];
+    if constexpr (HAS_V) v[t] = sv[pad(o + t)];
   }
   // odd-even transposition: swaps only strictly out-of-order neighbours, so
   // equal keys keep their order
@@ -139,27 +153,27 @@ __global__ void __launch_bounds__(kMsThreads) k_ms_tile(const K* src, const V* v
     __syncthreads();
 #pragma unroll
     for (int t = 0; t < kMsItems; ++t) {
-      sk[o + t] = k[t];
-      if constexpr (HAS_V) sv[o + t] = v[t];
+      sk[pad(o + t)] = k[t];
+      if constexpr (HAS_V) sv[pad(o + t)] = v[t];
     }
     __syncthreads();
     const uint32_t pair = o / (2 * w) * (2 * w);
     const uint32_t d = o - pair;
-    const K* a = sk + pair;
-    const K* b = a + w;
+    const Padded<K> a{sk, pair}, b{sk, pair + w};
+    const Padded<V> av{sv, pair}, bv{sv, pair + w};
     const uint32_t i = merge_path(a, w, b, w, d);
-    merge_items<K, V, HAS_V>(a, sv + pair, w, b, sv + pair + w, w, i, d - i, k, v);
+    merge_items<K, V, HAS_V>(a, av, w, b, bv, w, i, d - i, k, v);
   }
   __syncthreads();
 #pragma unroll
   for (int t = 0; t < kMsItems; ++t) {
-    sk[o + t] = k[t];
-    if constexpr (HAS_V) sv[o + t] = v[t];
+    sk[pad(o + t)] = k[t];
+    if constexpr (HAS_V) sv[pad(o + t)] = v[t];
   }
   __syncthreads();
   for (uint32_t i = tid; i < len; i += kMsThreads) {
-    dst[base + i] = sk[i];
-    if constexpr (HAS_V) vdst[base + i] = sv[i];
+    dst[base + i] = sk[pad(i)];
+    if constexpr (HAS_V) vdst[base + i] = sv[pad(i)];
   }
 }
 
@@ -206,11 +220,11 @@ __global__ void __launch_bounds__(kMsThreads) k_ms_merge(const K* __restrict__ s
   const int tid = threadIdx.x;
   for (uint32_t t = tid; t < la + lb; t += kMsThreads) {
     if (t < la) {
-      sk[t] = a[i0 + t];
-      if constexpr (HAS_V) sv[t] = vsrc[base + i0 + t];
+      sk[pad(t)] = a[i0 + t];
+      if constexpr (HAS_V) sv[pad(t)] = vsrc[base + i0 + t];
     } else {
-      sk[t] = b[j0 + t - la];
-      if constexpr (HAS_V) sv[t] = vsrc[base + na + j0 + t - la];
+      sk[pad(t)] = b[j0 + t - la];
+      if constexpr (HAS_V) sv[pad(t)] = vsrc[base + na + j0 + t - la];
     }
   }
   __syncthreads();
@@ -219,23 +233,25 @@ __global__ void __launch_bounds__(kMsThreads) k_ms_merge(const K* __restrict__ s
   const uint32_t o = uint32_t(tid) * kMsItems;
   const uint32_t total = la + lb;
   if (o < total) {
-    const uint32_t i = merge_path(sk, la, sk + la, lb, o);
-    merge_items<K, V, HAS_V>(sk, sv, la, sk + la, sv + la, lb, i, o - i, k, v);
+    const Padded<K> ra{sk, 0u}, rb{sk, la};
+    const Padded<V> rav{sv, 0u}, rbv{sv, la};
+    const uint32_t i = merge_path(ra, la, rb, lb, o);
+    merge_items<K, V, HAS_V>(ra, rav, la, rb, rbv, lb, i, o - i, k, v);
   }
   __syncthreads();
   if (o < total) {
 #pragma unroll
     for (int t = 0; t < kMsItems; ++t) {
       if (o + t < total) {
-        sk[o + t] = k[t];
-        if constexpr (HAS_V) sv[o + t] = v[t];
+        sk[pad(o + t)] = k[t];
+        if constexpr (HAS_V) sv[pad(o + t)] = v[t];
       }
     }
   }
   __syncthreads();
   for (uint32_t t = tid; t < total; t += kMsThreads) {
-    dst[p0 + t] = sk[t];
-    if constexpr (HAS_V) vdst[p0 + t] = sv[t];
+    dst[p0 + t] = sk[pad(t)];
+    if constexpr (HAS_V) vdst[p0 + t] = sv[pad(t)];
   }
 }
 

@@ -14,8 +14,8 @@ torch = pytest.importorskip("torch")
 from paper_1511_03404_gb300 import rs  # noqa: E402
 
 pytestmark = pytest.mark.gpu
-TILE = 2048
-SIZES = (0, 1, 2, 7, TILE - 1, TILE, TILE + 1, 3 * TILE + 5, 2**17 + 3, 2**20 + 7)
+TILE = 4096
+SIZES = (0, 1, 2, 7, 2047, 2049, TILE - 1, TILE, TILE + 1, 3 * TILE + 5, 2**17 + 3, 2**20 + 7)
 
 
 def make(kb, dist, n):

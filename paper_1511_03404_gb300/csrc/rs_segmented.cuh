@@ -36,9 +36,10 @@ struct SegDesc {
 };
 static_assert(sizeof(SegDesc) == 32, "SegDesc is 32 bytes");
 
-// Per long segment: histogram ticket, ready flag, exec mask, done counters.
+// Per long segment: histogram ticket, ready word (bit 0: the histograms are
+// scanned; bits 1..: the mask of passes that move data), done counters.
 constexpr int kSegStateWords = 16;
-enum SegStateField { kSegTicket = 0, kSegReady = 1, kSegExec = 2, kSegDone0 = 3 };
+enum SegStateField { kSegTicket = 0, kSegReady = 1, kSegDone0 = 3 };
 
 // Plan results in Ctrl::tile_counter[]
 enum SegCtrlField {
@@ -284,10 +285,12 @@ __global__ void __launch_bounds__(THREADS, 4)
         for (uint32_t i = tid; i < words; i += THREADS)
           st[lb_index<RADIX>(d.tile0 + t_first + i / RADIX, i % RADIX)] = 0u;
       }
-      __threadfence();
       __syncthreads();
       uint32_t* state = a.state + size_t(li) * kSegStateWords;
       if (tid == 0) {
+        // the CTA's counts and cleared words (ordered before by the barrier)
+        // become visible before the ticket
+        __threadfence();
         const uint32_t chunks = (d.len + CHUNK - 1) / CHUNK;
         s_misc[2] = atomicAdd(&state[kSegTicket], 1u) == chunks - 1u;
       }
@@ -308,9 +311,8 @@ __global__ void __launch_bounds__(THREADS, 4)
             const uint32_t skipped = ~exec & ((1u << passes) - 1u);
             exec |= skipped & (0u - skipped);
           }
-          state[kSegExec] = exec;
           __threadfence();
-          st_release(&state[kSegReady], 1u);
+          st_release(&state[kSegReady], 1u | (exec << 1));
         }
       }
     } else {
@@ -323,11 +325,21 @@ __global__ void __launch_bounds__(THREADS, 4)
       uint32_t* state = a.state + size_t(li) * kSegStateWords;
       const uint32_t ntiles = (d.len + TILE - 1) / TILE;
       if (tid == 0) {
-        bool ok = wait_geq(&state[kSegReady], 1u, ctrl, a.knobs.timeout_ns, gt);
-        if (ok && p > 0) ok = wait_geq(&state[kSegDone0 + p - 1], ntiles, ctrl,
-                                       a.knobs.timeout_ns, gt);
+        // both conditions read at once (one round trip); the bounded waits
+        // only when one of them does not hold yet
+        uint32_t ready = ld_relaxed(&state[kSegReady]);
+        const uint32_t done = p > 0 ? ld_relaxed(&state[kSegDone0 + p - 1]) : ntiles;
+        bool ok = (ready & 1u) && done >= ntiles;
+        if (ok) {
+          __threadfence();  // acquire: the histograms and the previous pass's output
+        } else {
+          ok = wait_geq(&state[kSegReady], 1u, ctrl, a.knobs.timeout_ns, gt);
+          if (ok && p > 0) ok = wait_geq(&state[kSegDone0 + p - 1], ntiles, ctrl,
+                                         a.knobs.timeout_ns, gt);
+          ready = ld_acquire(&state[kSegReady]);
+        }
         s_misc[3] = ok ? 1u : 0u;
-        s_misc[4] = ld_relaxed(&state[kSegExec]);
+        s_misc[4] = ready >> 1;
       }
       __syncthreads();
       const uint32_t exec = s_misc[4];
@@ -362,10 +374,12 @@ __global__ void __launch_bounds__(THREADS, 4)
         t.xout = false;
         onesweep_tile<K, VB, RADIX_BITS, THREADS, ITEMS, true>(t, ctrl, a.knobs.timeout_ns,
                                                                smem);
-        __threadfence();
       }
       __syncthreads();
-      if (tid == 0) atomicAdd(&state[kSegDone0 + p], 1u);
+      if (tid == 0) {
+        __threadfence();  // the tile's output, ordered before by the barrier, then the count
+        atomicAdd(&state[kSegDone0 + p], 1u);
+      }
     }
     __syncthreads();
   }

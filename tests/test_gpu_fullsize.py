@@ -87,3 +87,17 @@ def test_u64_pairs_2p27(dist):
     k = inputs.keys(np.uint64, dist, 1 << 27)
     src, out_k, out_v = run(8, 8, k)
     check_pairs(src, out_k, out_v)
+
+
+@pytest.mark.parametrize("vb", [0, 4], ids=["keys", "pairs"])
+def test_largest_array(vb):
+    """n = RS_MAX_N = 2^30 - 1: the look-back counts use their full 30 bits."""
+    n = rs.RS_MAX_N
+    k = inputs.keys(np.uint32, "uniform", n, seed=5)
+    src, out_k, out_v = run(4, vb, k)
+    del k
+    if vb:
+        check_pairs(src, out_k, out_v)
+    else:
+        want = ordered(torch.sort(ordered(src)).values)
+        assert bool((out_k == want).all())

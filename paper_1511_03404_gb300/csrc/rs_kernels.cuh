@@ -691,16 +691,13 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
   __syncthreads();
   stamp(t.trace, 2);
 
-  // ---- per digit: exclusive prefix over warps, tile count, publish the count
+  // ---- per digit: tile count, publish it; then the exclusive prefix over
+  // warps, which starts at the digit's first slot in the tile
   uint32_t my_cnt = 0u;
   if (tid < RADIX) {
     uint32_t run = 0u;
 #pragma unroll
-    for (int w = 0; w < WARPS; ++w) {
-      const uint32_t c = s_wh[w * RADIX + tid];
-      s_wh[w * RADIX + tid] = run;
-      run += c;
-    }
+    for (int w = 0; w < WARPS; ++w) run += s_wh[w * RADIX + tid];
     my_cnt = run;
     if (!t.silent) {
       st_relaxed(&t.status[lb_index<RADIX>(t.tile0 + tile, tid)],
@@ -713,9 +710,14 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
   if (tid < RADIX) {
     s_cnt[tid] = my_cnt;
     s_tstart[tid] = my_start;
+    uint32_t run = my_start;
+#pragma unroll
+    for (int w = 0; w < WARPS; ++w) {
+      const uint32_t c = s_wh[w * RADIX + tid];
+      s_wh[w * RADIX + tid] = run;
+      run += c;
+    }
   }
-  __syncthreads();
-  for (int i = tid; i < WARPS * RADIX; i += THREADS) s_wh[i] += s_tstart[i & (RADIX - 1)];
   __syncthreads();
   stamp(t.trace, 3);
 

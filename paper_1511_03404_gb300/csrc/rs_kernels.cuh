@@ -685,8 +685,13 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
   // item j of lane l is slot w*ITEMS*32 + j*32 + l
   const uint32_t slot0 = uint32_t(warp * ITEMS * 32 + lane);
   uint32_t dp[ITEMS];  // digit << 16 | rank in the warp
+  K kreg[VB > 0 ? 1 : ITEMS];  // keys only: the keys stay in registers until staged
 #pragma unroll
-  for (int j = 0; j < ITEMS; ++j) dp[j] = digit_of(s_kin[slot0 + j * 32], t.shift, t.mask);
+  for (int j = 0; j < ITEMS; ++j) {
+    const K k = s_kin[slot0 + j * 32];
+    if constexpr (VB == 0) kreg[j] = k;
+    dp[j] = digit_of(k, t.shift, t.mask);
+  }
   warp_rank_packed<ITEMS>(dp, s_wh + warp * RADIX, s_mm + warp * RADIX, lane);
   __syncthreads();
   stamp(t.trace, 2);
@@ -727,7 +732,10 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
 #pragma unroll
   for (int j = 0; j < ITEMS; ++j) {
     const uint32_t p = (dp[j] & 0xffffu) + s_wh[warp * RADIX + (dp[j] >> 16)];
-    s_out[p] = s_kin[slot0 + j * 32];
+    if constexpr (VB == 0)
+      s_out[p] = kreg[j];
+    else
+      s_out[p] = s_kin[slot0 + j * 32];
     if constexpr (VB > 0) pos[j] = p;
   }
   stamp(t.trace, 8);

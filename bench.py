@@ -335,7 +335,8 @@ def run_ours(args):
         "cpu_baseline": None,
         "e2e": {"value": e2e["value"], "unit": "Gkeys/s",
                 "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
-                "serial": e2e.get("serial"), "pipelining": e2e.get("pipelining")},
+                "serial": e2e.get("serial"), "link_bound": e2e.get("link_bound"),
+                "pipelining": e2e.get("pipelining")},
         "gpu_launches": launches,
         "clocks": clocks.summary(),
         "kernel_source": src,
@@ -388,65 +389,99 @@ def check_sorted(torch, k_out, v_out, k_in) -> bool:
 def e2e_rate(torch, rs, keys_h, vals_h, n, dev, ws, args, dists) -> dict:
     """Host -> device copy, sort, device -> host copy, per step, through the C ABI.
 
-    Two steps are in flight on two streams (two sets of device buffers and
-    workspaces, two sets of pinned host outputs), so that one step's copies
-    run while the other sorts; ``serial`` is the same with one stream."""
+    Three streams form a pipeline over three sets of device buffers and pinned
+    host outputs: the copy-in stream loads step i + 1 while the sort stream
+    sorts step i and the copy-out stream returns step i - 1; events order each
+    set's reuse.  ``serial`` is the same with one buffer set (no overlap), and
+    ``link_bound`` the step time the host link alone allows (both directions
+    at once, measured here)."""
     hk = {d: torch.from_numpy(keys_h[d].view(np.int32)).pin_memory() for d in dists}
     hv = torch.from_numpy(vals_h.view(np.int32)).pin_memory()
-    slots = []
-    for j in range(2):
+    nsets = 3
+    sets = []
+    for j in range(nsets):
         k = torch.empty(n, dtype=torch.int32, device=dev)
-        slots.append({
-            "stream": torch.cuda.Stream(dev),
+        sets.append({
             "k": k, "v": torch.empty_like(k), "ka": torch.empty_like(k), "va": torch.empty_like(k),
             "ok": torch.empty(n, dtype=torch.int32).pin_memory(),
             "ov": torch.empty(n, dtype=torch.int32).pin_memory(),
             "ws": ws if j == 0 else torch.empty_like(ws),
         })
+    s_in, s_sort, s_out = (torch.cuda.Stream(dev) for _ in range(3))
 
-    def step(i, sl):
-        d = dists[i % len(dists)]
-        with torch.cuda.stream(sl["stream"]):
-            h = sl["stream"].cuda_stream
-            sl["k"].copy_(hk[d], non_blocking=True)
-            sl["v"].copy_(hv, non_blocking=True)
-            st, in_alt = rs.rs_sort_pairs_u32(sl["k"].data_ptr(), sl["v"].data_ptr(),
-                                              sl["ka"].data_ptr(), sl["va"].data_ptr(), n, 0, 32,
-                                              sl["ws"].data_ptr(), sl["ws"].numel(), h)
-            rs.check(st, "rs_sort_pairs_u32")
-            sl["ok"].copy_(sl["ka"] if in_alt else sl["k"], non_blocking=True)
-            sl["ov"].copy_(sl["va"] if in_alt else sl["v"], non_blocking=True)
-
-    def timed(nslots):
-        steps = max(4, min(args.steps, 12))
-        for i in range(3):
-            step(i, slots[i % nslots])
+    def timed(nb, steps):
+        free = [None] * nb  # per set: the event after its last copy-out
         torch.cuda.synchronize()
-        s0 = slots[0]["stream"]
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
-        t0.record(s0)
-        for j in range(1, nslots):  # every stream starts after t0
-            slots[j]["stream"].wait_event(t0)
+        t0.record(s_in)
+        s_sort.wait_event(t0)
+        s_out.wait_event(t0)
         for i in range(steps):
-            step(i, slots[i % nslots])
-        for j in range(1, nslots):  # and t1 follows every stream's last step
-            e = torch.cuda.Event()
-            e.record(slots[j]["stream"])
-            s0.wait_event(e)
-        t1.record(s0)
+            d = dists[i % len(dists)]
+            sl = sets[i % nb]
+            if free[i % nb] is not None:
+                s_in.wait_event(free[i % nb])
+            with torch.cuda.stream(s_in):
+                sl["k"].copy_(hk[d], non_blocking=True)
+                sl["v"].copy_(hv, non_blocking=True)
+            loaded = torch.cuda.Event()
+            loaded.record(s_in)
+            s_sort.wait_event(loaded)
+            st, in_alt = rs.rs_sort_pairs_u32(sl["k"].data_ptr(), sl["v"].data_ptr(),
+                                              sl["ka"].data_ptr(), sl["va"].data_ptr(), n, 0, 32,
+                                              sl["ws"].data_ptr(), sl["ws"].numel(),
+                                              s_sort.cuda_stream)
+            rs.check(st, "rs_sort_pairs_u32")
+            sorted_ = torch.cuda.Event()
+            sorted_.record(s_sort)
+            s_out.wait_event(sorted_)
+            with torch.cuda.stream(s_out):
+                sl["ok"].copy_(sl["ka"] if in_alt else sl["k"], non_blocking=True)
+                sl["ov"].copy_(sl["va"] if in_alt else sl["v"], non_blocking=True)
+            free[i % nb] = torch.cuda.Event()
+            free[i % nb].record(s_out)
+        s_in.wait_stream(s_sort)
+        s_in.wait_stream(s_out)
+        t1.record(s_in)
         torch.cuda.synchronize()
+        # the last outputs are complete and sorted
+        last = sets[(steps - 1) % nb]
+        assert np.all(np.diff(last["ok"].numpy().view(np.uint32)) >= 0)
         return t0.elapsed_time(t1) / steps
 
-    ms_serial = timed(1)
-    ms = timed(2)
-    # the last outputs are complete and sorted
-    for sl in slots:
-        assert np.all(np.diff(sl["ok"].numpy().view(np.uint32)) >= 0)
+    def link_ms():
+        # one step's bytes in both directions at once, on two copy streams
+        a, b = sets[0], sets[1]
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(s_in)
+        s_out.wait_event(t0)
+        with torch.cuda.stream(s_in):
+            a["k"].copy_(hk[dists[0]], non_blocking=True)
+            a["v"].copy_(hv, non_blocking=True)
+        with torch.cuda.stream(s_out):
+            b["ok"].copy_(b["k"], non_blocking=True)
+            b["ov"].copy_(b["v"], non_blocking=True)
+        s_in.wait_stream(s_out)
+        t1.record(s_in)
+        torch.cuda.synchronize()
+        return t0.elapsed_time(t1)
+
+    steps = max(6, min(args.steps, 15))
+    timed(1, 2)
+    ms_serial = timed(1, max(4, steps // 2))
+    timed(nsets, nsets)
+    ms = timed(nsets, steps)
+    link = min(link_ms() for _ in range(3))
     return {"value": n / (ms / 1e3) / 1e9, "ms_per_step": ms, "h2d": 2 * 4 * n, "d2h": 2 * 4 * n,
             "serial": {"value": n / (ms_serial / 1e3) / 1e9, "ms_per_step": ms_serial},
-            "pipelining": "two steps in flight on two streams (copies of one overlap the other's "
-                          "sort); serial: one stream"}
+            "link_bound": {"value": n / (link / 1e3) / 1e9, "ms_per_step": link,
+                           "what": "the step's host->device and device->host bytes copied at once, "
+                                   "no sort"},
+            "pipelining": "three streams (copy-in, sort, copy-out) over three buffer sets: step "
+                          "i + 1 loads while step i sorts and step i - 1 returns; serial: one set"}
 
 
 def _time_sorts(torch, rs, kb, vb, keys, vals, reps, stream):

@@ -350,6 +350,13 @@ def run_ours(args):
         line["u64_2p27"] = bench_u64(torch, rs, dev)
         stage("segmented: batched vs plain")
         line["segmented"] = bench_segmented(torch, rs, dev, args.seg_scaled)
+        stage("merge sort and sample-sort partition, 2^26")
+        from paper_1511_03404_gb300 import workloads
+        line["merge_2p26"] = {"keys": workloads.merge(n, 4, 0, peak_gbs=hbm, device=dev.index or 0),
+                              "pairs": workloads.merge(n, 4, 4, peak_gbs=hbm,
+                                                       device=dev.index or 0)}
+        line["sample_partition_2p26"] = workloads.sample_partition(n, 64, 64, peak_gbs=hbm,
+                                                                   device=dev.index or 0)
     if not (args.no_cpu_baseline or args.quick):
         stage("cpu baseline (oracle)")
         line["cpu_baseline"] = cpu_oracle_rate(1 << 24)
@@ -696,6 +703,7 @@ def bench_serving(torch, rs, seconds: float = 10.0, rate: float = 5000.0,
     ring_bytes = 6 << 30
     ring = torch.empty(ring_bytes, dtype=torch.uint8).pin_memory()
     ring_base = ring.data_ptr()
+    link_before = host_link_gbs(torch, ring)
     st, srv = rs.rs_server_create(budget, streams)
     rs.check(st, "rs_server_create")
     pending = {}        # handle -> (ring start, ring end)
@@ -758,13 +766,44 @@ def bench_serving(torch, rs, seconds: float = 10.0, rate: float = 5000.0,
     rs.check(st, "rs_server_stats")
     rs.rs_server_destroy(srv)
     offered = float(sizes.sum()) / float(arrival[-1]) / 1e9
+    link_after = host_link_gbs(torch, ring)
     return {"requests": count, "rate_per_s": rate, "budget_gib": budget / 2**30,
             "streams": streams, "p50_ms": stats["p50_ms"], "p99_ms": stats["p99_ms"],
-            "max_ms": stats["max_ms"], "gkeys_per_s": stats["gkeys_per_s"],
+            "max_ms": stats["max_ms"], "wait_p99_ms": stats["wait_p99_ms"],
+            "service_p50_ms": stats["service_p50_ms"],
+            "service_p99_ms": stats["service_p99_ms"], "gkeys_per_s": stats["gkeys_per_s"],
             "offered_gkeys_per_s": offered, "batches": stats["batches"],
             "batched_requests": stats["batched_requests"], "max_queued": stats["max_queued"],
             "pool_peak_gib": stats["pool_peak_bytes"] / 2**30,
-            "latency": "submit -> completion callback, host pinned buffers in and out"}
+            "host_link_gb_per_s": {"before": link_before, "after": link_after,
+                                   "what": "256 MiB pinned copies, each direction alone"},
+            "latency": "submit -> completion callback, host pinned buffers in and out; wait = "
+                       "submit -> admission, service = admission -> completion"}
+
+
+def host_link_gbs(torch, host_u8) -> dict:
+    """Host<->device copy bandwidth (GB/s) right now, 256 MiB each way: the
+    serving latencies depend on it, and on a shared host it varies."""
+    nb = 256 << 20
+    dev_buf = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    h = host_u8[:nb]
+    out = {}
+    for name in ("h2d", "d2h"):
+        best = None
+        for _ in range(3):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            if name == "h2d":
+                dev_buf.copy_(h, non_blocking=True)
+            else:
+                h.copy_(dev_buf, non_blocking=True)
+            e1.record()
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1)
+            best = t if best is None else min(best, t)
+        out[name] = nb / (best / 1e3) / 1e9
+    return out
 
 
 def bench_serving_process(seconds: float) -> dict:

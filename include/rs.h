@@ -381,11 +381,41 @@ typedef struct rs_server_stats_t {
   double p50_ms, p99_ms, max_ms;      /* submit -> done latency of completed requests */
   double wall_s;                      /* first submit -> last completion */
   double gkeys_per_s;                 /* keys / wall_s / 1e9 */
+  double wait_p50_ms, wait_p99_ms;    /* submit -> admission (queueing) */
+  double service_p50_ms, service_p99_ms; /* admission -> done (copies, sort, callback) */
 } rs_server_stats_t;
+
+/* One completed request, as recorded by the server: times in seconds since
+ * the first submission after creation or the last rs_server_reset_stats. */
+typedef struct rs_trace_record {
+  double submit_s, admit_s, done_s; /* submitted, admitted to a stream, completion callback */
+  uint64_t n;                       /* elements */
+  int key_bytes, val_bytes;
+  int stream;                       /* server stream it ran on */
+  int batched;                      /* 1: shared a batched segmented launch */
+} rs_trace_record;
 
 /* Create a server: budget_bytes >= 1 MiB of device memory, 1..64 streams.
  * RS_ERR_NOMEM if the pool cannot be allocated. */
 rs_status rs_server_create(size_t budget_bytes, int streams, rs_server** out);
+
+/* Scheduling policy of a server (rs_server_get_config / rs_server_set_config).
+ * A new setting applies to admissions after the call; running units keep
+ * theirs.  Defaults in brackets. */
+typedef struct rs_server_config {
+  size_t batch_max_n;    /* u32 pair requests of 2..batch_max_n elements are batched [2^14] */
+  size_t max_batch_keys; /* elements per batched launch at most, >= batch_max_n [2^22] */
+  size_t large_n;        /* requests of at least large_n elements are "large" [2^21] */
+  int max_large;         /* large units admitted at once, oldest first, 1..64 [2] */
+  int large_low_priority; /* 1: large units run on low-priority streams, so that the
+                             kernels of short requests are scheduled ahead of them [1] */
+} rs_server_config;
+
+/* RS_ERR_INVALID for a NULL argument or a field out of range
+ * (batch_max_n > max_batch_keys, max_batch_keys > RS_MAX_N, large_n = 0,
+ * max_large outside 1..64, large_low_priority not 0 or 1). */
+rs_status rs_server_get_config(rs_server* server, rs_server_config* out);
+rs_status rs_server_set_config(rs_server* server, const rs_server_config* cfg);
 
 /* Stop the scheduler after the requests already on the GPU finish; queued
  * requests end as RS_ERR_CANCELLED.  Frees the pool and the streams. */
@@ -409,6 +439,14 @@ rs_status rs_cancel(rs_server* server, rs_handle handle);
 rs_status rs_server_stats(rs_server* server, rs_server_stats_t* out);
 rs_status rs_server_reset_stats(rs_server* server);
 
+/*
+ * Copy the records of completed requests (in completion order) into
+ * out[0 .. min(cap, total)); *total receives how many there are.  out may be
+ * NULL with cap 0 to ask for the count.  The server keeps every record until
+ * rs_server_reset_stats.
+ */
+rs_status rs_server_trace(rs_server* server, rs_trace_record* out, size_t cap, size_t* total);
+
 /* ---- per-kernel timing (CUDA events recorded on the sort's stream) ---- */
 
 /* Kinds of kernels the library launches. */
@@ -418,7 +456,8 @@ typedef enum rs_kernel_kind {
   RS_KERNEL_SMALL = 2,   /* whole array sorted by one CTA in shared memory */
   RS_KERNEL_SEGMENTED = 3, /* batched segments */
   RS_KERNEL_MERGE = 4,   /* merge sort: tile sort or one merge pass */
-  RS_KERNEL_KINDS = 5
+  RS_KERNEL_SAMPLE = 5,  /* sample-sort partition: bucket counts or the run copy */
+  RS_KERNEL_KINDS = 6
 } rs_kernel_kind;
 
 /*
@@ -432,7 +471,9 @@ rs_status rs_profile_begin(int capacity);
  * Stop recording, wait for the recorded events and return, per kernel kind,
  * the number of launches, their summed duration in milliseconds and their
  * summed algorithmic bytes (reads + writes the method needs: for a onesweep
- * pass 2 n (key bytes + value bytes), for the upsweep n key bytes).  Arrays
+ * pass 2 n (key bytes + value bytes), for the upsweep n key bytes, for a
+ * merge pass 2 n (key bytes + value bytes), for the sample-sort bucket
+ * counts n key bytes and for its run copy 2 n (key bytes + value bytes)).  Arrays
  * have RS_KERNEL_KINDS entries; any may be NULL.
  */
 rs_status rs_profile_end(int* launches, double* ms, double* bytes);

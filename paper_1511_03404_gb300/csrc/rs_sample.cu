@@ -273,12 +273,16 @@ rs_status partition(uint32_t* keys, uint32_t* vals, uint32_t* kout, uint32_t* vo
   auto* counts = reinterpret_cast<uint32_t*>(w + L.counts);
   auto* part = reinterpret_cast<uint32_t*>(w + L.part);
   const uint64_t cells = L.nblk * uint64_t(buckets);
+  prof_before(s);
   k_ss_count<<<unsigned(L.nblk), 1024, 0, s>>>(bk, n, L.nblk, spl, uint32_t(buckets), counts);
+  prof_after(s, RS_KERNEL_SAMPLE, double(n) * 4.0);
   k_scan_reduce<<<unsigned(L.parts), kScanThreads, 0, s>>>(counts, cells, part);
   k_scan_partials<<<1, kScanThreads, 0, s>>>(part, uint32_t(L.parts));
   k_scan_down<<<unsigned(L.parts), kScanThreads, 0, s>>>(counts, cells, part);
+  prof_before(s);
   k_ss_scatter<<<unsigned(L.nblk), 1024, 0, s>>>(bk, bv, kout, vout, n, L.nblk, spl,
                                                  uint32_t(buckets), counts);
+  prof_after(s, RS_KERNEL_SAMPLE, 2.0 * double(n) * 8.0);
   k_ss_bucket_offsets<<<grid_for(uint64_t(buckets) + 1, 256), 256, 0, s>>>(
       counts, L.nblk, uint32_t(buckets), n, d_off);
   if (d_spl && cudaMemcpyAsync(d_spl, spl, size_t(buckets - 1) * 4, cudaMemcpyDeviceToDevice,

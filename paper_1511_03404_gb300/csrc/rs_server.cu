@@ -83,7 +83,9 @@ struct Request {
   rs_request req{};
   int state = 0;  // 0 queued, 1 running, 2 done
   rs_status status = RS_OK;
-  double t_submit = 0, t_done = 0;
+  double t_submit = 0, t_admit = 0, t_done = 0;
+  int stream = -1;
+  bool batched = false;
 };
 
 struct Unit;  // one admitted sort or batch
@@ -97,7 +99,8 @@ struct rs_server {
   size_t budget = 0;
   char* pool_base = nullptr;
   std::unique_ptr<Pool> pool;
-  std::vector<cudaStream_t> streams;
+  std::vector<cudaStream_t> streams;     // high priority: short requests and batches
+  std::vector<cudaStream_t> streams_lo;  // low priority, same slots: large requests
   std::vector<int> stream_busy;
   size_t batch_max_n = 1u << 14;  // requests up to this size share a segmented launch
   size_t max_batch_keys = 1u << 22;
@@ -107,6 +110,7 @@ struct rs_server {
   // shorter requests keep the other streams.
   size_t large_n = size_t(1) << 21;
   int max_large = 2;
+  int large_low_priority = 1;
   int large_running = 0;
   std::mutex mu;
   std::condition_variable cv;
@@ -122,7 +126,7 @@ struct rs_server {
   bool stop = false;
   std::thread sched;
   // statistics
-  std::vector<double> latencies;
+  std::vector<rs_trace_record> trace;  // completed requests; times absolute (now_s)
   uint64_t completed = 0, failed = 0, keys_done = 0, batches = 0, batched_requests = 0;
   double first_submit = 0, last_done = 0;
   size_t max_queue = 0;
@@ -194,7 +198,8 @@ void CUDART_CB on_unit_done(void* p) {
 rs_status launch_single(rs_server* s, Unit* u) {
   Request& r = *u->members[0];
   const rs_request& q = r.req;
-  cudaStream_t st = s->streams[u->stream];
+  cudaStream_t st = (u->large && s->large_low_priority) ? s->streams_lo[u->stream]
+                                                        : s->streams[u->stream];
   char* base = s->pool_base + u->pool_off;
   const size_t kbytes = q.n * q.key_bytes, vbytes = q.n * q.val_bytes;
   const SingleLayout L = single_layout(q);
@@ -306,7 +311,16 @@ void finish_unit(rs_server* s, Unit* u, rs_status st) {
     if (m->status == RS_OK) {
       s->completed += 1;
       s->keys_done += m->req.n;
-      s->latencies.push_back(m->t_done - m->t_submit);
+      rs_trace_record rec{};
+      rec.submit_s = m->t_submit;
+      rec.admit_s = m->t_admit;
+      rec.done_s = m->t_done;
+      rec.n = m->req.n;
+      rec.key_bytes = m->req.key_bytes;
+      rec.val_bytes = m->req.val_bytes;
+      rec.stream = m->stream;
+      rec.batched = m->batched ? 1 : 0;
+      s->trace.push_back(rec);
       s->last_done = std::max(s->last_done, m->t_done);
     } else {
       s->failed += 1;
@@ -356,8 +370,11 @@ void scheduler(rs_server* s) {
       if (batchable(s, r->req)) {
         const bool same_bits = batch.empty() || (batch[0]->req.begin_bit == r->req.begin_bit &&
                                                  batch[0]->req.end_bit == r->req.end_bit);
+        // a batch never outgrows the pool, so that it is admitted once
+        // enough of the pool is free
         if (same_bits && batch_keys + r->req.n <= s->max_batch_keys &&
-            batch.size() < kMaxBatchMembers) {
+            batch.size() < kMaxBatchMembers &&
+            plan_batch(batch_keys + r->req.n, batch.size() + 1).bytes <= s->budget) {
           batch.push_back(r);
           batch_keys += r->req.n;
         } else {
@@ -391,6 +408,8 @@ void scheduler(rs_server* s) {
       *u->h_status = 0u;
       s->stream_busy[si] = 1;
       r->state = 1;
+      r->t_admit = now_s();
+      r->stream = si;
       launches.push_back(Launch{u, false, BatchPlan{}});
     }
     if (!batch.empty()) {
@@ -409,7 +428,13 @@ void scheduler(rs_server* s) {
         u->h_status = s->status_slab + si;
         *u->h_status = 0u;
         s->stream_busy[si] = 1;
-        for (auto& m : batch) m->state = 1;
+        const double t = now_s();
+        for (auto& m : batch) {
+          m->state = 1;
+          m->t_admit = t;
+          m->stream = si;
+          m->batched = true;
+        }
         s->batches += 1;
         s->batched_requests += batch.size();
         launches.push_back(Launch{u, true, b});
@@ -462,13 +487,23 @@ rs_status rs_server_create(size_t budget_bytes, int streams, rs_server** out) {
     delete s;
     return RS_ERR_NOMEM;
   }
-  s->streams.resize(streams);
+  s->streams.assign(streams, nullptr);
+  s->streams_lo.assign(streams, nullptr);
   s->stream_busy.assign(streams, 0);
-  for (auto& st : s->streams) {
-    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
-      st = nullptr;
-      for (auto& t : s->streams)
-        if (t) cudaStreamDestroy(t);
+  int least = 0, greatest = 0;  // numerically: greatest < least
+  if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
+    cudaGetLastError();
+    least = greatest = 0;
+  }
+  for (int i = 0; i < streams; ++i) {
+    if (cudaStreamCreateWithPriority(&s->streams[i], cudaStreamNonBlocking, greatest) !=
+            cudaSuccess ||
+        cudaStreamCreateWithPriority(&s->streams_lo[i], cudaStreamNonBlocking, least) !=
+            cudaSuccess) {
+      cudaGetLastError();
+      for (auto* v : {&s->streams, &s->streams_lo})
+        for (auto& t : *v)
+          if (t) cudaStreamDestroy(t);
       cudaFree(s->pool_base);
       cudaFreeHost(s->status_slab);
       cudaFreeHost(s->off_slab);
@@ -499,6 +534,7 @@ rs_status rs_server_destroy(rs_server* s) {
   s->cv.notify_all();
   if (s->sched.joinable()) s->sched.join();
   for (auto& st : s->streams) cudaStreamDestroy(st);
+  for (auto& st : s->streams_lo) cudaStreamDestroy(st);
   cudaFree(s->pool_base);
   cudaFreeHost(s->status_slab);
   cudaFreeHost(s->off_slab);
@@ -506,9 +542,41 @@ rs_status rs_server_destroy(rs_server* s) {
   return RS_OK;
 }
 
+rs_status rs_server_get_config(rs_server* s, rs_server_config* out) {
+  if (!s || !out) return RS_ERR_INVALID;
+  std::lock_guard<std::mutex> g(s->mu);
+  out->batch_max_n = s->batch_max_n;
+  out->max_batch_keys = s->max_batch_keys;
+  out->large_n = s->large_n;
+  out->max_large = s->max_large;
+  out->large_low_priority = s->large_low_priority;
+  return RS_OK;
+}
+
+rs_status rs_server_set_config(rs_server* s, const rs_server_config* c) {
+  if (!s || !c) return RS_ERR_INVALID;
+  if (c->batch_max_n > c->max_batch_keys || c->max_batch_keys > RS_MAX_N || c->large_n == 0 ||
+      c->max_large < 1 || c->max_large > 64 ||
+      (c->large_low_priority != 0 && c->large_low_priority != 1))
+    return RS_ERR_INVALID;
+  {
+    std::lock_guard<std::mutex> g(s->mu);
+    s->batch_max_n = c->batch_max_n;
+    s->max_batch_keys = c->max_batch_keys;
+    s->large_n = c->large_n;
+    s->max_large = c->max_large;
+    s->large_low_priority = c->large_low_priority;
+    s->changes += 1;  // the scheduler looks at the queue again
+  }
+  s->cv.notify_all();
+  return RS_OK;
+}
+
 rs_status rs_submit(rs_server* s, const rs_request* req, rs_handle* out) {
   if (!s || !req || !out || !valid_request(*req)) return RS_ERR_INVALID;
-  const size_t need = batchable(s, *req) ? plan_batch(req->n, 1).bytes : single_footprint(*req);
+  // whichever way the policy at admission runs it, it must fit the pool
+  const bool pair32 = req->key_bytes == 4 && req->val_bytes == 4;
+  const size_t need = std::max(single_footprint(*req), pair32 ? plan_batch(req->n, 1).bytes : 0);
   if (need > s->budget) return RS_ERR_INVALID;  // could never be admitted
   auto r = std::make_shared<Request>();
   r->req = *req;
@@ -568,16 +636,24 @@ rs_status rs_server_stats(rs_server* s, rs_server_stats_t* out) {
   out->max_queued = s->max_queue;
   out->pool_peak_bytes = s->pool->peak();
   out->pool_used_bytes = s->pool->used();
-  if (!s->latencies.empty()) {
-    std::vector<double> l = s->latencies;
-    std::sort(l.begin(), l.end());
-    auto pct = [&](double p) {
+  if (!s->trace.empty()) {
+    // percentile p of the interval b - a over the records, in ms
+    auto pct = [&](double rs_trace_record::*a, double rs_trace_record::*b, double p) {
+      std::vector<double> l;
+      l.reserve(s->trace.size());
+      for (const auto& r : s->trace) l.push_back(r.*b - r.*a);
+      std::sort(l.begin(), l.end());
       const size_t i = std::min(l.size() - 1, size_t(p * double(l.size() - 1) + 0.5));
       return l[i] * 1e3;
     };
-    out->p50_ms = pct(0.50);
-    out->p99_ms = pct(0.99);
-    out->max_ms = l.back() * 1e3;
+    using T = rs_trace_record;
+    out->p50_ms = pct(&T::submit_s, &T::done_s, 0.50);
+    out->p99_ms = pct(&T::submit_s, &T::done_s, 0.99);
+    out->max_ms = pct(&T::submit_s, &T::done_s, 1.0);
+    out->wait_p50_ms = pct(&T::submit_s, &T::admit_s, 0.50);
+    out->wait_p99_ms = pct(&T::submit_s, &T::admit_s, 0.99);
+    out->service_p50_ms = pct(&T::admit_s, &T::done_s, 0.50);
+    out->service_p99_ms = pct(&T::admit_s, &T::done_s, 0.99);
   }
   const double span = s->last_done - s->first_submit;
   out->wall_s = span > 0 ? span : 0;
@@ -585,10 +661,27 @@ rs_status rs_server_stats(rs_server* s, rs_server_stats_t* out) {
   return RS_OK;
 }
 
+rs_status rs_server_trace(rs_server* s, rs_trace_record* out, size_t cap, size_t* total) {
+  if (!s || !total || (cap && !out)) return RS_ERR_INVALID;
+  std::lock_guard<std::mutex> g(s->mu);
+  *total = s->trace.size();
+  double t0 = s->first_submit;
+  if (t0 == 0)
+    for (const auto& r : s->trace) t0 = (t0 == 0 || r.submit_s < t0) ? r.submit_s : t0;
+  const size_t m = std::min(cap, s->trace.size());
+  for (size_t i = 0; i < m; ++i) {
+    out[i] = s->trace[i];
+    out[i].submit_s -= t0;
+    out[i].admit_s -= t0;
+    out[i].done_s -= t0;
+  }
+  return RS_OK;
+}
+
 rs_status rs_server_reset_stats(rs_server* s) {
   if (!s) return RS_ERR_INVALID;
   std::lock_guard<std::mutex> g(s->mu);
-  s->latencies.clear();
+  s->trace.clear();
   s->completed = s->failed = s->keys_done = s->batches = s->batched_requests = 0;
   s->first_submit = s->last_done = 0;
   s->max_queue = s->pending.size();

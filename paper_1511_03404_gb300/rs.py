@@ -29,10 +29,10 @@ RS_ERR_CANCELLED = 8
 RS_ERR_NOT_FOUND = 9
 RS_MAX_N = (1 << 30) - 1
 
-RS_KERNEL_UPSWEEP, RS_KERNEL_ONESWEEP, RS_KERNEL_SMALL, RS_KERNEL_SEGMENTED, RS_KERNEL_MERGE = \
-    range(5)
-RS_KERNEL_KINDS = 5
-KERNEL_NAMES = ("upsweep", "onesweep", "small", "segmented", "merge")
+(RS_KERNEL_UPSWEEP, RS_KERNEL_ONESWEEP, RS_KERNEL_SMALL, RS_KERNEL_SEGMENTED, RS_KERNEL_MERGE,
+ RS_KERNEL_SAMPLE) = range(6)
+RS_KERNEL_KINDS = 6
+KERNEL_NAMES = ("upsweep", "onesweep", "small", "segmented", "merge", "sample")
 
 (RS_DEBUG_TIMEOUT_NS, RS_DEBUG_DROP_PUBLISH_TILE, RS_DEBUG_DROP_PUBLISH_PASS, RS_DEBUG_TRACE_PTR,
  RS_DEBUG_TRACE_TILES, RS_DEBUG_TRACE_PASS, RS_DEBUG_LB_SMALL) = range(7)
@@ -63,7 +63,22 @@ class rs_server_stats_t(ctypes.Structure):
                 ("max_queued", ctypes.c_uint64), ("pool_peak_bytes", ctypes.c_size_t),
                 ("pool_used_bytes", ctypes.c_size_t), ("p50_ms", ctypes.c_double),
                 ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
-                ("wall_s", ctypes.c_double), ("gkeys_per_s", ctypes.c_double)]
+                ("wall_s", ctypes.c_double), ("gkeys_per_s", ctypes.c_double),
+                ("wait_p50_ms", ctypes.c_double), ("wait_p99_ms", ctypes.c_double),
+                ("service_p50_ms", ctypes.c_double), ("service_p99_ms", ctypes.c_double)]
+
+
+class rs_server_config(ctypes.Structure):
+    _fields_ = [("batch_max_n", ctypes.c_size_t), ("max_batch_keys", ctypes.c_size_t),
+                ("large_n", ctypes.c_size_t), ("max_large", ctypes.c_int),
+                ("large_low_priority", ctypes.c_int)]
+
+
+class rs_trace_record(ctypes.Structure):
+    _fields_ = [("submit_s", ctypes.c_double), ("admit_s", ctypes.c_double),
+                ("done_s", ctypes.c_double), ("n", ctypes.c_uint64),
+                ("key_bytes", ctypes.c_int), ("val_bytes", ctypes.c_int),
+                ("stream", ctypes.c_int), ("batched", ctypes.c_int)]
 
 
 _lock = threading.Lock()
@@ -100,6 +115,9 @@ _SIGS = {
     "rs_cancel": ([_vp, ctypes.c_uint64], _i),
     "rs_server_stats": ([_vp, _vp], _i),
     "rs_server_reset_stats": ([_vp], _i),
+    "rs_server_trace": ([_vp, _vp, _sz, _vp], _i),
+    "rs_server_get_config": ([_vp, _vp], _i),
+    "rs_server_set_config": ([_vp, _vp], _i),
     "rs_tune_set": ([_i, _i, _sz, _i], _i),
     "rs_tune_clear": ([], _i),
     "rs_profile_begin": ([_i], _i),
@@ -348,6 +366,28 @@ def rs_server_stats(server):
 
 def rs_server_reset_stats(server) -> int:
     return load().rs_server_reset_stats(server)
+
+
+def rs_server_get_config(server):
+    out = rs_server_config()
+    st = load().rs_server_get_config(server, ctypes.byref(out))
+    return st, {name: getattr(out, name) for name, _ in rs_server_config._fields_}
+
+
+def rs_server_set_config(server, cfg: dict) -> int:
+    return load().rs_server_set_config(server, ctypes.byref(rs_server_config(**cfg)))
+
+
+def rs_server_trace(server):
+    """(status, list of per-request dicts) for every completed request."""
+    total = ctypes.c_size_t()
+    st = load().rs_server_trace(server, None, 0, ctypes.byref(total))
+    if st != RS_OK:
+        return st, []
+    buf = (rs_trace_record * max(total.value, 1))()
+    st = load().rs_server_trace(server, buf, total.value, ctypes.byref(total))
+    names = [name for name, _ in rs_trace_record._fields_]
+    return st, [{k: getattr(buf[i], k) for k in names} for i in range(min(total.value, len(buf)))]
 
 
 def rs_tune_set(key_bytes: int, val_bytes: int, n_max: int, variant: int) -> int:

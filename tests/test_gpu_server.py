@@ -100,6 +100,17 @@ def test_mixed_trace_matches_oracle(server):
     assert stats["completed"] == len(reqs) and stats["failed"] == 0
     assert stats["batches"] >= 1  # the short u32 pair requests shared launches
     assert stats["p99_ms"] >= stats["p50_ms"] > 0
+    assert stats["service_p99_ms"] >= stats["service_p50_ms"] > 0
+    assert stats["wait_p99_ms"] >= stats["wait_p50_ms"] >= 0
+    # the per-request trace: one record per request, times in order
+    st, trace = rs.rs_server_trace(server)
+    rs.check(st, "rs_server_trace")
+    assert len(trace) == len(reqs)
+    assert sorted(t["n"] for t in trace) == sorted(int(k.size) for k, _ in reqs)
+    for t in trace:
+        assert 0 <= t["submit_s"] <= t["admit_s"] <= t["done_s"]
+        assert 0 <= t["stream"] < 8 and t["batched"] in (0, 1)
+    assert any(t["batched"] for t in trace)
 
 
 def test_same_result_alone_and_in_the_mix():
@@ -152,5 +163,41 @@ def test_rejections_and_cancel():
         for h, i in handles.items():
             if status[i] == rs.RS_OK:
                 assert np.array_equal(reqs[i].ok, np.sort(reqs[i].k))
+    finally:
+        rs.rs_server_destroy(srv)
+
+
+def test_config_policies_same_results():
+    """Every scheduling policy gives the oracle's results: no batching, every
+    request large with one at a time, and large requests on default-priority
+    streams."""
+    reqs = make_trace(40, seed=21, max_log2=17)
+    st, srv = rs.rs_server_create(1 << 30, 4)
+    rs.check(st)
+    try:
+        st, cfg = rs.rs_server_get_config(srv)
+        rs.check(st)
+        assert cfg == {"batch_max_n": 1 << 14, "max_batch_keys": 1 << 22, "large_n": 1 << 21,
+                       "max_large": 2, "large_low_priority": 1}
+        for bad in ({"batch_max_n": 1 << 23}, {"max_batch_keys": (1 << 30) + 1},
+                    {"large_n": 0}, {"max_large": 0}, {"max_large": 65},
+                    {"large_low_priority": 2}):
+            assert rs.rs_server_set_config(srv, dict(cfg, **bad)) == rs.RS_ERR_INVALID
+        assert rs.rs_server_get_config(srv)[1] == cfg  # a rejected setting changes nothing
+        for policy in ({"batch_max_n": 0},
+                       {"large_n": 1, "max_large": 1},
+                       {"large_n": 1 << 12, "large_low_priority": 0}):
+            rs.check(rs.rs_server_set_config(srv, dict(cfg, **policy)), "rs_server_set_config")
+            rs.check(rs.rs_server_reset_stats(srv))
+            out = run(srv, reqs)
+            for r in out:
+                ek, ev = oracle.lsd_sort(r.k, r.v)
+                assert np.array_equal(r.ok, ek)
+                if r.v is not None:
+                    assert np.array_equal(r.ov, ev)
+            st, stats = rs.rs_server_stats(srv)
+            assert stats["completed"] == len(reqs)
+            if policy.get("batch_max_n") == 0:
+                assert stats["batches"] == 0
     finally:
         rs.rs_server_destroy(srv)

@@ -161,6 +161,21 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
 }
 
+// Shared memory of one short-segment sort: the warps' counters and peer
+// masks, and the segment's keys and values, each in a buffer of its own.
+template <class K, int VB, int RADIX_BITS, int THREADS, int ITEMS>
+struct SegSmallSmem {
+  static constexpr int RADIX = 1 << RADIX_BITS;
+  static constexpr int WARPS = THREADS / 32;
+  static constexpr int TILE = THREADS * ITEMS;
+  static constexpr int WH = 0;                        // u32 [WARPS][RADIX] warp counters
+  static constexpr int MM = WH + WARPS * RADIX * 4;   // u32 [WARPS][RADIX] peer masks
+  static constexpr int TOT = MM + WARPS * RADIX * 4;  // u32 [32]
+  static constexpr int KEYS = (TOT + 32 * 4 + 15) / 16 * 16;  // K [TILE]
+  static constexpr int VALS = KEYS + TILE * int(sizeof(K));   // V [TILE]
+  static constexpr int BYTES = VALS + (VB > 0 ? TILE * VB : 0);
+};
+
 template <class K, int VB, int RADIX_BITS, int THREADS, int ITEMS, int CHUNK_TILES>
 struct SegKernelCfg {
   static constexpr int RADIX = 1 << RADIX_BITS;
@@ -171,7 +186,7 @@ struct SegKernelCfg {
   static constexpr int HIST_SLOTS = 16;
   static constexpr int HIST_BYTES = MAXP * (RADIX / 2) * HIST_SLOTS * 4;
   using OS = OnesweepSmem<K, VB, RADIX_BITS, THREADS, ITEMS>;
-  using SS = SmallSmem<K, VB, RADIX_BITS, THREADS, ITEMS>;
+  using SS = SegSmallSmem<K, VB, RADIX_BITS, THREADS, ITEMS>;
   static constexpr int A = OS::BYTES;
   static constexpr int BODY = A > HIST_BYTES ? A : HIST_BYTES;
   static constexpr int MISC = (BODY + 15) / 16 * 16;  // u32 [8]
@@ -194,8 +209,87 @@ struct SegArgs {
   Knobs knobs;
 };
 
+// Every digit pass (Sec. 2.6) of one segment of len <= TILE elements inside
+// one CTA.  The segment lives in shared memory from the first load to the
+// last store; a pass reads each thread's items from it, ranks them, and
+// writes them back at their stable positions (a barrier separates the reads
+// from the writes), keys first, then values.  So no more than one item array
+// and the positions are live in registers at a time, and four CTAs fit on an
+// SM.  Past the end the keys are the largest key: they rank after every real
+// key in every pass and are never written out.
 template <class K, int VB, int RADIX_BITS, int THREADS, int ITEMS>
-__global__ void __launch_bounds__(THREADS, 1)
+__device__ __forceinline__ void seg_cta_sort(const K* kin, const ValT<VB>* vin, K* kout,
+                                             ValT<VB>* vout, uint32_t len, int begin_bit,
+                                             int end_bit, unsigned char* smem) {
+  using V = ValT<VB>;
+  using S = SegSmallSmem<K, VB, RADIX_BITS, THREADS, ITEMS>;
+  constexpr int RADIX = S::RADIX, WARPS = S::WARPS, TILE = S::TILE;
+  uint32_t* s_wh = reinterpret_cast<uint32_t*>(smem + S::WH);
+  uint32_t* s_mm = reinterpret_cast<uint32_t*>(smem + S::MM);
+  uint32_t* s_tot = reinterpret_cast<uint32_t*>(smem + S::TOT);
+  K* s_k = reinterpret_cast<K*>(smem + S::KEYS);
+  V* s_v = reinterpret_cast<V*>(smem + S::VALS);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t slot0 = uint32_t(warp * ITEMS * 32 + lane);
+
+  for (uint32_t i = tid; i < uint32_t(TILE); i += THREADS) {
+    s_k[i] = i < len ? kin[i] : ~K(0);
+    if constexpr (VB > 0) s_v[i] = i < len ? vin[i] : V(0);
+  }
+  for (int lo = begin_bit; lo < end_bit; lo += RADIX_BITS) {
+    const uint32_t shift = uint32_t(lo);
+    const uint32_t mask = (1u << (min(lo + RADIX_BITS, end_bit) - lo)) - 1u;
+    for (int i = tid; i < 2 * WARPS * RADIX; i += THREADS) s_wh[i] = 0u;  // counters + masks
+    __syncthreads();
+    K key[ITEMS];
+    uint32_t dp[ITEMS];  // digit << 16 | rank in the warp, then the item's position
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+      key[j] = s_k[slot0 + j * 32];
+      dp[j] = digit_of(key[j], shift, mask);
+    }
+    warp_rank_packed<ITEMS>(dp, s_wh + warp * RADIX, s_mm + warp * RADIX, lane);
+    __syncthreads();
+    // per digit: exclusive prefix over the warps, from the digit's start
+    uint32_t cnt = 0u;
+    if (tid < RADIX) {
+#pragma unroll
+      for (int w = 0; w < WARPS; ++w) cnt += s_wh[w * RADIX + tid];
+    }
+    const uint32_t start = block_exclusive_scan<THREADS>(cnt, s_tot);
+    if (tid < RADIX) {
+      uint32_t run = start;
+#pragma unroll
+      for (int w = 0; w < WARPS; ++w) {
+        const uint32_t c = s_wh[w * RADIX + tid];
+        s_wh[w * RADIX + tid] = run;
+        run += c;
+      }
+    }
+    __syncthreads();  // every key of the pass was read above
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+      dp[j] = (dp[j] & 0xffffu) + s_wh[warp * RADIX + (dp[j] >> 16)];
+      s_k[dp[j]] = key[j];
+    }
+    if constexpr (VB > 0) {
+      V val[ITEMS];
+#pragma unroll
+      for (int j = 0; j < ITEMS; ++j) val[j] = s_v[slot0 + j * 32];
+      __syncthreads();  // every value was read
+#pragma unroll
+      for (int j = 0; j < ITEMS; ++j) s_v[dp[j]] = val[j];
+    }
+    __syncthreads();
+  }
+  for (uint32_t i = tid; i < len; i += THREADS) {
+    kout[i] = s_k[i];
+    if constexpr (VB > 0) vout[i] = s_v[i];
+  }
+}
+
+template <class K, int VB, int RADIX_BITS, int THREADS, int ITEMS>
+__global__ void __launch_bounds__(THREADS, 4)
     k_seg_small(K* __restrict__ k0, ValT<VB>* __restrict__ v0, K* __restrict__ k1,
                 ValT<VB>* __restrict__ v1, SegArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -207,8 +301,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     const uint32_t s = a.small_ids[i];
     const uint64_t b = a.off[s];
     const uint32_t len = uint32_t(a.off[s + 1] - b);
-    cta_sort<K, VB, RADIX_BITS, THREADS, ITEMS>(k0 + b, v0 + b, kout + b, vout + b, len,
-                                                a.begin_bit, a.end_bit, smem, KeyXf<K>{});
+    seg_cta_sort<K, VB, RADIX_BITS, THREADS, ITEMS>(k0 + b, v0 + b, kout + b, vout + b, len,
+                                                    a.begin_bit, a.end_bit, smem);
     __syncthreads();
   }
 }

@@ -355,70 +355,38 @@ void scheduler(rs_server* s) {
       BatchPlan plan;
     };
     std::vector<Launch> launches;
-    std::vector<std::shared_ptr<Request>> batch;
-    size_t batch_keys = 0;
-    std::vector<uint64_t> keep;  // looked at, still queued, in order
-    int looked = 0;
-    bool large_blocked = false;  // large requests are admitted in submission order
-    while (!s->pending.empty() && looked < 256) {
+    std::vector<uint64_t> keep;  // looked at, still queued
+    std::vector<std::shared_ptr<Request>> seen;  // taken off the queue front, in order
+    while (!s->pending.empty() && seen.size() < 256) {
       const uint64_t id = s->pending.front();
       s->pending.pop_front();
       auto found = s->reqs.find(id);
-      if (found == s->reqs.end()) continue;
-      ++looked;
-      std::shared_ptr<Request> r = found->second;
-      if (batchable(s, r->req)) {
-        const bool same_bits = batch.empty() || (batch[0]->req.begin_bit == r->req.begin_bit &&
-                                                 batch[0]->req.end_bit == r->req.end_bit);
-        // a batch never outgrows the pool, so that it is admitted once
-        // enough of the pool is free
-        if (same_bits && batch_keys + r->req.n <= s->max_batch_keys &&
-            batch.size() < kMaxBatchMembers &&
-            plan_batch(batch_keys + r->req.n, batch.size() + 1).bytes <= s->budget) {
-          batch.push_back(r);
-          batch_keys += r->req.n;
-        } else {
-          keep.push_back(id);
-        }
-        continue;
+      if (found != s->reqs.end()) seen.push_back(found->second);
+    }
+    // 1. Short requests first: the oldest batchable ones form one batch,
+    //    which takes a free stream before any single request does.  Taken
+    //    after the singles, it found every freed stream gone to the steady
+    //    flow of medium requests, and short requests waited tens of ms.
+    std::vector<std::shared_ptr<Request>> batch;
+    size_t batch_keys = 0;
+    for (auto& r : seen) {
+      if (!batchable(s, r->req)) continue;
+      const bool same_bits = batch.empty() || (batch[0]->req.begin_bit == r->req.begin_bit &&
+                                               batch[0]->req.end_bit == r->req.end_bit);
+      // a batch never outgrows the pool, so that it is admitted once enough
+      // of the pool is free
+      if (same_bits && batch_keys + r->req.n <= s->max_batch_keys &&
+          batch.size() < kMaxBatchMembers &&
+          plan_batch(batch_keys + r->req.n, batch.size() + 1).bytes <= s->budget) {
+        batch.push_back(r);
+        batch_keys += r->req.n;
       }
-      const bool large = r->req.n >= s->large_n;
-      if (large && (large_blocked || s->large_running >= s->max_large)) {
-        large_blocked = true;  // later large requests wait behind this one
-        keep.push_back(id);
-        continue;
-      }
-      const int si = free_stream(s);
-      size_t off = 0;
-      const size_t need = single_footprint(r->req);
-      if (si < 0 || !s->pool->alloc(need, &off)) {
-        if (large) large_blocked = true;
-        keep.push_back(id);
-        continue;
-      }
-      Unit* u = new Unit;
-      u->srv = s;
-      u->large = large;
-      if (large) s->large_running += 1;
-      u->members.push_back(r);
-      u->pool_off = off;
-      u->pool_bytes = rs::align_up(std::max<size_t>(need, 256), 256);
-      u->stream = si;
-      u->h_status = s->status_slab + si;
-      *u->h_status = 0u;
-      s->stream_busy[si] = 1;
-      r->state = 1;
-      r->t_admit = now_s();
-      r->stream = si;
-      launches.push_back(Launch{u, false, BatchPlan{}});
     }
     if (!batch.empty()) {
       const int si = free_stream(s);
       const BatchPlan b = plan_batch(batch_keys, batch.size());
       size_t off = 0;
-      if (si < 0 || !s->pool->alloc(b.bytes, &off)) {
-        for (auto& m : batch) keep.push_back(m->id);  // no room yet
-      } else {
+      if (si >= 0 && s->pool->alloc(b.bytes, &off)) {
         Unit* u = new Unit;
         u->srv = s;
         u->members = batch;
@@ -439,6 +407,44 @@ void scheduler(rs_server* s) {
         s->batched_requests += batch.size();
         launches.push_back(Launch{u, true, b});
       }
+    }
+    // 2. Single requests in submission order.
+    bool large_blocked = false;  // large requests are admitted in submission order
+    for (auto& r : seen) {
+      if (r->state != 0) continue;  // in the batch just formed
+      if (batchable(s, r->req)) {  // waits for a later batch
+        keep.push_back(r->id);
+        continue;
+      }
+      const bool large = r->req.n >= s->large_n;
+      if (large && (large_blocked || s->large_running >= s->max_large)) {
+        large_blocked = true;  // later large requests wait behind this one
+        keep.push_back(r->id);
+        continue;
+      }
+      const int si = free_stream(s);
+      size_t off = 0;
+      const size_t need = single_footprint(r->req);
+      if (si < 0 || !s->pool->alloc(need, &off)) {
+        if (large) large_blocked = true;
+        keep.push_back(r->id);
+        continue;
+      }
+      Unit* u = new Unit;
+      u->srv = s;
+      u->large = large;
+      if (large) s->large_running += 1;
+      u->members.push_back(r);
+      u->pool_off = off;
+      u->pool_bytes = rs::align_up(std::max<size_t>(need, 256), 256);
+      u->stream = si;
+      u->h_status = s->status_slab + si;
+      *u->h_status = 0u;
+      s->stream_busy[si] = 1;
+      r->state = 1;
+      r->t_admit = now_s();
+      r->stream = si;
+      launches.push_back(Launch{u, false, BatchPlan{}});
     }
     if (keep.size() > 1)
       std::sort(keep.begin(), keep.end());  // ids grow with submission order

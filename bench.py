@@ -21,7 +21,6 @@ import argparse
 import faulthandler
 import gc
 import hashlib
-import itertools
 import json
 import os
 import statistics
@@ -724,14 +723,16 @@ def bench_serving(torch, rs, seconds: float = 10.0, rate: float = 5000.0,
             poll_some(block=True)
 
     def poll_some(block=False):
-        # the oldest requests first, a bounded number per call, so that the
-        # submission loop keeps to the arrival schedule when many are in flight
-        for hnd in list(itertools.islice(pending, 64)):
+        # one call takes every finished handle off the server's completion
+        # queue; polling each pending handle instead kept the server's lock
+        # busy and starved its scheduler thread
+        st_, finished = rs.rs_server_completed(srv, 4096)
+        rs.check(st_, "rs_server_completed")
+        for hnd in finished:
             st_, done = rs.rs_poll(srv, hnd)
-            if done:
-                if st_ != rs.RS_OK:
-                    raise SystemExit(f"bench: server request failed: {rs.status_string(st_)}")
-                live.remove(pending.pop(hnd))
+            if st_ != rs.RS_OK or not done:
+                raise SystemExit(f"bench: server request failed: {rs.status_string(st_)}")
+            live.remove(pending.pop(hnd))
         if block and pending:
             time.sleep(0.0002)
 
@@ -742,8 +743,13 @@ def bench_serving(torch, rs, seconds: float = 10.0, rate: float = 5000.0,
     gc.disable()
     t0 = time.perf_counter()
     for i in range(count):
-        while time.perf_counter() - t0 < arrival[i]:
+        while True:
+            rem = arrival[i] - (time.perf_counter() - t0)
+            if rem <= 0:
+                break
             poll_some()
+            if rem > 3e-4:
+                time.sleep(1e-4)  # far from the next arrival: leave the lock alone
         n = int(sizes[i])
         o = int(offsets[i])
         if is_pairs[i]:

@@ -435,6 +435,15 @@ rs_status rs_poll(rs_server* server, rs_handle handle, int* done);
 /* Cancel a request that has not started (RS_ERR_BUSY once it is on the GPU). */
 rs_status rs_cancel(rs_server* server, rs_handle handle);
 
+/* Completion queue: move up to `cap` handles of requests that finished (done,
+ * failed or cancelled) since the last call, oldest first, into out[0 .. *count).
+ * rs_poll on such a handle then reports its status without waiting.  One call
+ * replaces polling every pending handle, so a client with many requests in
+ * flight does not contend with the scheduler for the server's lock.  The
+ * queue holds at most 2^20 handles; older ones are dropped (rs_poll still
+ * finds them). */
+rs_status rs_server_completed(rs_server* server, rs_handle* out, size_t cap, size_t* count);
+
 /* Latency percentiles, throughput and pool use since creation or the last reset. */
 rs_status rs_server_stats(rs_server* server, rs_server_stats_t* out);
 rs_status rs_server_reset_stats(rs_server* server);

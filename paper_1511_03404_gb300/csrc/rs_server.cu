@@ -127,6 +127,7 @@ struct rs_server {
   std::thread sched;
   // statistics
   std::vector<rs_trace_record> trace;  // completed requests; times absolute (now_s)
+  std::deque<uint64_t> completed_ids;  // finished, not yet taken by rs_server_completed
   uint64_t completed = 0, failed = 0, keys_done = 0, batches = 0, batched_requests = 0;
   double first_submit = 0, last_done = 0;
   size_t max_queue = 0;
@@ -294,6 +295,14 @@ int free_stream(rs_server* s) {
   return -1;
 }
 
+constexpr size_t kMaxCompletedQueue = size_t(1) << 20;
+
+void note_completed(rs_server* s, uint64_t id) {
+  // caller holds s->mu
+  if (s->completed_ids.size() >= kMaxCompletedQueue) s->completed_ids.pop_front();
+  s->completed_ids.push_back(id);
+}
+
 void finish_unit(rs_server* s, Unit* u, rs_status st) {
   // caller holds s->mu
   s->pool->release(u->pool_off, u->pool_bytes);
@@ -307,6 +316,7 @@ void finish_unit(rs_server* s, Unit* u, rs_status st) {
   for (auto& m : u->members) {
     m->state = 2;
     m->status = st != RS_OK ? st : dev;
+    note_completed(s, m->id);
     if (m->t_done == 0) m->t_done = now_s();
     if (m->status == RS_OK) {
       s->completed += 1;
@@ -625,7 +635,20 @@ rs_status rs_cancel(rs_server* s, rs_handle h) {
   if (q != s->pending.end()) s->pending.erase(q);
   it->second->state = 2;
   it->second->status = RS_ERR_CANCELLED;
+  note_completed(s, h);
   s->changes += 1;
+  return RS_OK;
+}
+
+rs_status rs_server_completed(rs_server* s, rs_handle* out, size_t cap, size_t* count) {
+  if (!s || !count || (cap && !out)) return RS_ERR_INVALID;
+  std::lock_guard<std::mutex> g(s->mu);
+  size_t k = 0;
+  while (k < cap && !s->completed_ids.empty()) {
+    out[k++] = s->completed_ids.front();
+    s->completed_ids.pop_front();
+  }
+  *count = k;
   return RS_OK;
 }
 

@@ -117,6 +117,7 @@ _SIGS = {
     "rs_server_reset_stats": ([_vp], _i),
     "rs_server_trace": ([_vp, _vp, _sz, _vp], _i),
     "rs_server_get_config": ([_vp, _vp], _i),
+    "rs_server_completed": ([_vp, _vp, _sz, _vp], _i),
     "rs_server_set_config": ([_vp, _vp], _i),
     "rs_tune_set": ([_i, _i, _sz, _i], _i),
     "rs_tune_clear": ([], _i),
@@ -366,6 +367,14 @@ def rs_server_stats(server):
 
 def rs_server_reset_stats(server) -> int:
     return load().rs_server_reset_stats(server)
+
+
+def rs_server_completed(server, cap: int = 1024):
+    """(status, handles of requests finished since the last call, oldest first)."""
+    buf = (ctypes.c_uint64 * max(cap, 1))()
+    count = ctypes.c_size_t()
+    st = load().rs_server_completed(server, buf, cap, ctypes.byref(count))
+    return st, [buf[i] for i in range(count.value)]
 
 
 def rs_server_get_config(server):

@@ -201,3 +201,31 @@ def test_config_policies_same_results():
                 assert stats["batches"] == 0
     finally:
         rs.rs_server_destroy(srv)
+
+
+def test_completion_queue(server):
+    """rs_server_completed hands out every finished request once, and
+    rs_poll then reports its status."""
+    reqs = make_trace(30, seed=5, max_log2=16)
+    out = [Req(k, v) for k, v in reqs]
+    handles = {}
+    for i, r in enumerate(out):
+        st, h = rs.rs_submit(server, r.c)
+        rs.check(st, "rs_submit")
+        handles[h] = i
+    seen = []
+    t0 = time.time()
+    while len(seen) < len(handles):
+        st, fin = rs.rs_server_completed(server, 7)
+        rs.check(st, "rs_server_completed")
+        assert len(fin) <= 7
+        seen += fin
+        if time.time() - t0 > 120:
+            raise TimeoutError("requests not done")
+        time.sleep(0.0005)
+    assert sorted(seen) == sorted(handles)  # each exactly once
+    for h in seen:
+        assert rs.rs_poll(server, h) == (rs.RS_OK, True)
+    assert rs.rs_server_completed(server, 8) == (rs.RS_OK, [])
+    for r in out:
+        assert np.array_equal(r.ok, oracle.lsd_sort(r.k, r.v)[0])

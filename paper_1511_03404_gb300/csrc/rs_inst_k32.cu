@@ -18,6 +18,8 @@ const Variant* variants_k32(int* count) {
       FusedSort<uint32_t, 0, 8, 256, 16, 4>::describe(),
       FusedSort<uint32_t, 0, 8, 256, 8, 4>::describe(),
       ClusterSort<uint32_t, 0, 8, 512, 16, 8>::describe(),
+      OnesweepSort<uint32_t, 0, 8, 256, 15, 4, true, 16>::describe(),
+      OnesweepSort<uint32_t, 0, 8, 256, 17, 4, true, 16>::describe(),
   };
   *count = int(sizeof(table) / sizeof(table[0]));
   return table;

@@ -124,6 +124,34 @@ __device__ __forceinline__ void warp_rank_packed(uint32_t (&dp)[ITEMS], uint32_t
   }
 }
 
+// Rank within half-warp units: lanes 0-15 and lanes 16-31 of a warp rank
+// their items separately, each half against its own counter words.  A word
+// holds the half's running count of the digit in its upper 16 bits and the
+// peer mask of the current item (one bit per lane of the half) in its lower
+// 16 bits, so an item costs a shared atomic OR, a load and the leader's store
+// (the leader's store clears the mask and advances the count at once).  wh
+// points at the half's own [RADIX] words; dp as in warp_rank_packed.
+template <int ITEMS>
+__device__ __forceinline__ void half_rank_packed(uint32_t (&dp)[ITEMS], uint32_t* wh, int lane) {
+  static_assert(ITEMS * 16 < 65536, "counts fit 16 bits");
+  const uint32_t sub = uint32_t(lane & 15);
+  const uint32_t bit = 1u << sub;
+  const uint32_t lt = bit - 1u;
+#pragma unroll
+  for (int j = 0; j < ITEMS; ++j) {
+    const uint32_t d = dp[j];
+    atomicOr(&wh[d], bit);
+    __syncwarp();
+    const uint32_t v = wh[d];
+    __syncwarp();
+    const uint32_t peers = v & 0xffffu;
+    const uint32_t before = v >> 16;
+    if (sub == uint32_t(31 - __clz(peers))) wh[d] = (before + uint32_t(__popc(peers))) << 16;
+    __syncwarp();  // the next item's atomics come after the leader's store
+    dp[j] = (d << 16) | (before + uint32_t(__popc(peers & lt)));
+  }
+}
+
 template <class K>
 __device__ __forceinline__ uint32_t digit_of(K key, uint32_t shift, uint32_t mask) {
   return static_cast<uint32_t>(key >> shift) & mask;
@@ -349,14 +377,18 @@ __global__ void __launch_bounds__(THREADS, 1)
 
 // -------------------------------------------------------------- onesweep
 
-template <class K, int VB, int RADIX_BITS, int THREADS, int ITEMS>
+// UNIT: lanes per ranking unit, 32 (a warp, warp_rank_packed) or 16 (half a
+// warp, half_rank_packed).
+template <class K, int VB, int RADIX_BITS, int THREADS, int ITEMS, int UNIT = 32>
 struct OnesweepSmem {
+  static_assert(UNIT == 32 || UNIT == 16, "warp or half-warp ranking units");
   static constexpr int RADIX = 1 << RADIX_BITS;
   static constexpr int WARPS = THREADS / 32;
+  static constexpr int UNITS = THREADS / UNIT;
   static constexpr int TILE = THREADS * ITEMS;
   static constexpr int ELEM = (int(sizeof(K)) > VB) ? int(sizeof(K)) : VB;
-  static constexpr int WH = 0;                              // u32 [WARPS][RADIX] warp counters
-  static constexpr int CNT = WH + WARPS * RADIX * 4;       // u32 [RADIX] tile counts
+  static constexpr int WH = 0;                              // u32 [UNITS][RADIX] unit counters
+  static constexpr int CNT = WH + UNITS * RADIX * 4;       // u32 [RADIX] tile counts
   static constexpr int TSTART = CNT + RADIX * 4;           // u32 [RADIX] tile digit starts
   static constexpr int GBASE = TSTART + RADIX * 4;         // u32 [RADIX] global base
   static constexpr int TOT = GBASE + RADIX * 4;            // u32 [32]
@@ -623,14 +655,15 @@ struct Prefetch {
 // and as soon as the key buffer is free again this call takes the next tile
 // id (s_misc[3]) and starts staging its keys (s_misc[4] = 1), overlapping the
 // end of this tile.
-template <class K, int VB, int RADIX_BITS, int THREADS, int ITEMS, bool CG, bool PERSIST = false>
+template <class K, int VB, int RADIX_BITS, int THREADS, int ITEMS, bool CG, bool PERSIST = false,
+          int UNIT = 32>
 __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ctrl,
                                               uint64_t timeout_ns, unsigned char* smem,
                                               uint32_t parity = 0u,
                                               const Prefetch* pf = nullptr) {
   using V = ValT<VB>;
-  using S = OnesweepSmem<K, VB, RADIX_BITS, THREADS, ITEMS>;
-  constexpr int RADIX = S::RADIX, WARPS = S::WARPS, TILE = S::TILE;
+  using S = OnesweepSmem<K, VB, RADIX_BITS, THREADS, ITEMS, UNIT>;
+  constexpr int RADIX = S::RADIX, WARPS = S::WARPS, UNITS = S::UNITS, TILE = S::TILE;
   static_assert(RADIX <= THREADS, "one thread per digit");
   static_assert(TILE <= 65536, "stage slots fit 16 bits");
   uint32_t* s_wh = reinterpret_cast<uint32_t*>(smem + S::WH);
@@ -660,9 +693,13 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
   }
   if (tid == 0) s_misc[1] = 0u;
   K* s_kin = Stage<K>(t.ksrc + tile_base, tile_len).at(smem + S::KIN);
-  for (int i = tid; i < WARPS * RADIX; i += THREADS) {
-    s_wh[i] = 0u;
-    s_mm[i] = 0u;
+  if constexpr (UNIT == 32) {
+    for (int i = tid; i < WARPS * RADIX; i += THREADS) {
+      s_wh[i] = 0u;
+      s_mm[i] = 0u;
+    }
+  } else {
+    for (int i = tid; i < UNITS * RADIX; i += THREADS) s_wh[i] = 0u;
   }
   bool landed = mbar_wait_bounded(&s_bar[0], parity, ctrl, timeout_ns, tile);
   if (!landed) landed = mbar_wait_bounded(&s_bar[0], parity, ctrl, timeout_ns, tile);
@@ -681,28 +718,35 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
   }
   stamp(t.trace, 1);
 
-  // ---- rank within the warp: warp w owns tile slots [w*ITEMS*32, (w+1)*ITEMS*32),
-  // item j of lane l is slot w*ITEMS*32 + j*32 + l
-  const uint32_t slot0 = uint32_t(warp * ITEMS * 32 + lane);
-  uint32_t dp[ITEMS];  // digit << 16 | rank in the warp
+  // ---- rank within the unit: unit u owns tile slots [u*ITEMS*UNIT, (u+1)*ITEMS*UNIT),
+  // item j of the unit's lane l is slot u*ITEMS*UNIT + j*UNIT + l.  (With
+  // half-warp units and ITEMS odd, the two halves of a warp read 16 banks
+  // apart.)
+  const int unit = tid / UNIT;
+  const uint32_t slot0 = uint32_t(unit * ITEMS * UNIT + (tid % UNIT));
+  uint32_t dp[ITEMS];  // digit << 16 | rank in the unit
   K kreg[VB > 0 ? 1 : ITEMS];  // keys only: the keys stay in registers until staged
 #pragma unroll
   for (int j = 0; j < ITEMS; ++j) {
-    const K k = s_kin[slot0 + j * 32];
+    const K k = s_kin[slot0 + j * UNIT];
     if constexpr (VB == 0) kreg[j] = k;
     dp[j] = digit_of(k, t.shift, t.mask);
   }
-  warp_rank_packed<ITEMS>(dp, s_wh + warp * RADIX, s_mm + warp * RADIX, lane);
+  if constexpr (UNIT == 32)
+    warp_rank_packed<ITEMS>(dp, s_wh + warp * RADIX, s_mm + warp * RADIX, lane);
+  else
+    half_rank_packed<ITEMS>(dp, s_wh + unit * RADIX, lane);
   __syncthreads();
   stamp(t.trace, 2);
 
   // ---- per digit: tile count, publish it; then the exclusive prefix over
   // warps, which starts at the digit's first slot in the tile
   uint32_t my_cnt = 0u;
+  constexpr int CSHIFT = UNIT == 32 ? 0 : 16;  // where the unit counters keep the count
   if (tid < RADIX) {
     uint32_t run = 0u;
 #pragma unroll
-    for (int w = 0; w < WARPS; ++w) run += s_wh[w * RADIX + tid];
+    for (int w = 0; w < UNITS; ++w) run += s_wh[w * RADIX + tid] >> CSHIFT;
     my_cnt = run;
     if (!t.silent) {
       st_relaxed(&t.status[lb_index<RADIX>(t.tile0 + tile, tid)],
@@ -717,8 +761,8 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
     s_tstart[tid] = my_start;
     uint32_t run = my_start;
 #pragma unroll
-    for (int w = 0; w < WARPS; ++w) {
-      const uint32_t c = s_wh[w * RADIX + tid];
+    for (int w = 0; w < UNITS; ++w) {
+      const uint32_t c = s_wh[w * RADIX + tid] >> CSHIFT;
       s_wh[w * RADIX + tid] = run;
       run += c;
     }
@@ -731,11 +775,11 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
   uint32_t pos[VB > 0 ? ITEMS : 1];  // stage slots, for the values
 #pragma unroll
   for (int j = 0; j < ITEMS; ++j) {
-    const uint32_t p = (dp[j] & 0xffffu) + s_wh[warp * RADIX + (dp[j] >> 16)];
+    const uint32_t p = (dp[j] & 0xffffu) + s_wh[unit * RADIX + (dp[j] >> 16)];
     if constexpr (VB == 0)
       s_out[p] = kreg[j];
     else
-      s_out[p] = s_kin[slot0 + j * 32];
+      s_out[p] = s_kin[slot0 + j * UNIT];
     if constexpr (VB > 0) pos[j] = p;
   }
   stamp(t.trace, 8);
@@ -919,7 +963,7 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
     if (!__syncthreads_or(!ok)) {
       V* s_vout = reinterpret_cast<V*>(smem + S::OUT);
 #pragma unroll
-      for (int j = 0; j < ITEMS; ++j) s_vout[pos[j]] = s_vin[slot0 + j * 32];
+      for (int j = 0; j < ITEMS; ++j) s_vout[pos[j]] = s_vin[slot0 + j * UNIT];
       if constexpr (PERSIST) {
         // the key buffer is free (values are staged in OUT): start the next tile
         if (tid == 0) {
@@ -960,14 +1004,14 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
 // One digit pass, one tile per CTA.  The grid has one CTA per tile; tile ids
 // come from an atomic counter so that a tile's predecessors have always
 // started before it (forward progress of the look-back).
-template <class K, int VB, int RADIX_BITS, int THREADS, int ITEMS, int MINB>
+template <class K, int VB, int RADIX_BITS, int THREADS, int ITEMS, int MINB, int UNIT = 32>
 __global__ void __launch_bounds__(THREADS, MINB)
     k_onesweep(K* __restrict__ k0, K* __restrict__ k1, ValT<VB>* __restrict__ v0,
                ValT<VB>* __restrict__ v1, uint32_t n, int pass, uint32_t shift, uint32_t mask,
                const uint32_t* __restrict__ pass_offsets, uint32_t* __restrict__ status,
                uint32_t* __restrict__ gagg, uint32_t* __restrict__ ginc, uint32_t tiles,
                Ctrl* __restrict__ ctrl, Knobs knobs, KeyXf<K> xf) {
-  using S = OnesweepSmem<K, VB, RADIX_BITS, THREADS, ITEMS>;
+  using S = OnesweepSmem<K, VB, RADIX_BITS, THREADS, ITEMS, UNIT>;
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t* s_misc = reinterpret_cast<uint32_t*>(smem + S::MISC);
 
@@ -1003,7 +1047,8 @@ __global__ void __launch_bounds__(THREADS, MINB)
   t.xf = xf;
   t.xin = xf.on && pass == __ffs(int(exec)) - 1;  // first and last pass that move data
   t.xout = xf.on && pass == 31 - __clz(exec);
-  onesweep_tile<K, VB, RADIX_BITS, THREADS, ITEMS, false>(t, ctrl, knobs.timeout_ns, smem);
+  onesweep_tile<K, VB, RADIX_BITS, THREADS, ITEMS, false, false, UNIT>(t, ctrl, knobs.timeout_ns,
+                                                                      smem);
 }
 
 // One digit pass with resident CTAs (a grid of SMs x resident CTAs): each CTA
@@ -1011,7 +1056,7 @@ __global__ void __launch_bounds__(THREADS, MINB)
 // loading its next tile while it finishes the current one.  Tile ids are
 // still taken in order by running CTAs, so the look-back keeps making
 // progress: the lowest unfinished tile is always being worked on.
-template <class K, int VB, int RADIX_BITS, int THREADS, int ITEMS, int MINB>
+template <class K, int VB, int RADIX_BITS, int THREADS, int ITEMS, int MINB, int UNIT = 32>
 __global__ void __launch_bounds__(THREADS, MINB)
     k_onesweep_persist(K* __restrict__ k0, K* __restrict__ k1, ValT<VB>* __restrict__ v0,
                        ValT<VB>* __restrict__ v1, uint32_t n, int pass, uint32_t shift,
@@ -1019,7 +1064,7 @@ __global__ void __launch_bounds__(THREADS, MINB)
                        uint32_t* __restrict__ status, uint32_t* __restrict__ gagg,
                        uint32_t* __restrict__ ginc, uint32_t tiles, Ctrl* __restrict__ ctrl,
                        Knobs knobs, KeyXf<K> xf) {
-  using S = OnesweepSmem<K, VB, RADIX_BITS, THREADS, ITEMS>;
+  using S = OnesweepSmem<K, VB, RADIX_BITS, THREADS, ITEMS, UNIT>;
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t* s_misc = reinterpret_cast<uint32_t*>(smem + S::MISC);
   uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem + S::MBAR);
@@ -1066,7 +1111,7 @@ __global__ void __launch_bounds__(THREADS, MINB)
     t.trace = (knobs.trace != nullptr && pass == knobs.trace_pass && tile < knobs.trace_tiles)
                   ? knobs.trace + size_t(tile) * 16
                   : nullptr;
-    const bool ok = onesweep_tile<K, VB, RADIX_BITS, THREADS, ITEMS, false, true>(
+    const bool ok = onesweep_tile<K, VB, RADIX_BITS, THREADS, ITEMS, false, true, UNIT>(
         t, ctrl, knobs.timeout_ns, smem, it & 1u, &pf);
     __syncthreads();
     const bool next = s_misc[4] != 0u;

@@ -14,14 +14,16 @@
 namespace rs {
 
 // PERSIST: the passes run as k_onesweep_persist on a grid of SMs x resident
-// CTAs instead of one CTA per tile.
-template <class K, int VB, int R, int THREADS, int ITEMS, int MINB, bool PERSIST = false>
+// CTAs instead of one CTA per tile.  UNIT: lanes per ranking unit (32: warps,
+// 16: half warps).
+template <class K, int VB, int R, int THREADS, int ITEMS, int MINB, bool PERSIST = false,
+          int UNIT = 32>
 struct OnesweepSort {
   static constexpr int RADIX = 1 << R;
   static constexpr int TILE = THREADS * ITEMS;
   static constexpr int UP_THREADS = 1024;
   static constexpr int MAXP = (8 * int(sizeof(K)) + R - 1) / R;
-  using S = OnesweepSmem<K, VB, R, THREADS, ITEMS>;
+  using S = OnesweepSmem<K, VB, R, THREADS, ITEMS, UNIT>;
 
   static size_t tiles(uint32_t n) { return (size_t(n) + TILE - 1) / TILE; }
 
@@ -70,8 +72,8 @@ struct OnesweepSort {
     const int slot = prof_note_mask(a.stream, &ctrl->exec_mask);
     using V = ValT<VB>;
     auto kern = [] {  // instantiate only the kernel this variant launches
-      if constexpr (PERSIST) return &k_onesweep_persist<K, VB, R, THREADS, ITEMS, MINB>;
-      else return &k_onesweep<K, VB, R, THREADS, ITEMS, MINB>;
+      if constexpr (PERSIST) return &k_onesweep_persist<K, VB, R, THREADS, ITEMS, MINB, UNIT>;
+      else return &k_onesweep<K, VB, R, THREADS, ITEMS, MINB, UNIT>;
     }();
     const int occ = prepare_kernel(reinterpret_cast<const void*>(kern), THREADS, S::BYTES);
     if (occ <= 0) return cudaErrorInvalidConfiguration;

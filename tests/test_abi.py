@@ -64,7 +64,8 @@ def test_workspace_sizes():
     assert st == rs.RS_OK and b == 0
     st, b = rs.rs_workspace_bytes(4, 4, 1000, 0, 32)  # one-CTA path: no workspace
     assert st == rs.RS_OK and b == 0
-    st, b1 = rs.rs_workspace_bytes(4, 4, 2**26, 0, 32)
+    # variant 0 named explicitly: the tuned table may pick another tile shape
+    st, b1 = rs.rs_workspace_bytes(4, 4, 2**26, 0, 32, variant=0)
     assert st == rs.RS_OK
     # onesweep: 256 B control + counts + offsets + look-back words of every
     # pass (per tile, plus two per group of 32 tiles)

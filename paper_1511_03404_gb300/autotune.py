@@ -5,8 +5,10 @@ For every (key bytes, value bytes) and every size n of the sweep, each
 compiled variant that can sort n is timed on uniform keys (median of a few
 CUDA-event timed sorts, inputs restored before each, outside the events).
 The fastest variant of size n becomes the table entry "n_max = n"; a sort of
-m elements then uses the entry with the smallest n_max >= m (above every
-entry the library's built-in choice applies).  The table is written to
+m elements then uses the entry with the smallest n_max >= m.  The variant of
+the largest size swept also gets an entry up to the largest sortable array,
+so that larger sorts keep the tile shape that won at the top of the sweep
+(without it the library's built-in choice would apply there).  The table is written to
 ``tuned.json`` next to this file, which the binding loads at start-up.
 
     python -m paper_1511_03404_gb300.autotune [--quick] [--out PATH]
@@ -98,9 +100,24 @@ def tune(sizes=SIZES, types=TYPES, reps=5, log=print, verbose=False) -> dict:
                 f"({infos[best]}) {results[best]:.4f} ms")
             del keys, vals
         torch.cuda.empty_cache()
+        extend_to_max(entries, kb, vb, infos)
     return {"device": torch.cuda.get_device_name(dev), "sizes": list(sizes),
             "entries": entries,
             "method": "median of %d CUDA-event timed sorts of uniform keys per variant" % reps}
+
+
+def extend_to_max(entries: list, kb: int, vb: int, infos: list) -> None:
+    """Append an entry n_max = RS_MAX_N for (kb, vb) that repeats the variant of
+    the largest size swept, when that variant sorts arrays of any size."""
+    mine = [e for e in entries if e["key_bytes"] == kb and e["val_bytes"] == vb]
+    if not mine:
+        return
+    top = max(mine, key=lambda e: e["n_max"])
+    if top["n_max"] >= rs.RS_MAX_N or infos[top["variant"]]["max_n"] < rs.RS_MAX_N:
+        return
+    entries.append({"key_bytes": kb, "val_bytes": vb, "n_max": rs.RS_MAX_N,
+                    "variant": top["variant"], "ms": None, "gkeys_per_s": None,
+                    "extrapolated_from": top["n_max"], "variant_info": top["variant_info"]})
 
 
 def main(argv=None):

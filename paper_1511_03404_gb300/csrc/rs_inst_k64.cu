@@ -14,6 +14,8 @@ const Variant* variants_k64(int* count) {
       OnesweepSort<uint64_t, 0, 8, 256, 12, 3, true>::describe(),
       FusedSort<uint64_t, 0, 8, 256, 12, 3>::describe(),
       ClusterSort<uint64_t, 0, 8, 512, 16, 8>::describe(),
+      OnesweepSort<uint64_t, 0, 8, 256, 13, 3, true, 16>::describe(),
+      OnesweepSort<uint64_t, 0, 8, 256, 11, 3, true, 16>::describe(),
   };
   *count = int(sizeof(table) / sizeof(table[0]));
   return table;

@@ -14,6 +14,8 @@ const Variant* variants_kv64(int* count) {
       OnesweepSort<uint64_t, 8, 8, 256, 12, 2, true>::describe(),
       FusedSort<uint64_t, 8, 8, 256, 12, 2>::describe(),
       ClusterSort<uint64_t, 8, 8, 512, 8, 8>::describe(),
+      OnesweepSort<uint64_t, 8, 8, 256, 13, 2, false, 16>::describe(),
+      OnesweepSort<uint64_t, 8, 8, 256, 11, 2, false, 16>::describe(),
   };
   *count = int(sizeof(table) / sizeof(table[0]));
   return table;

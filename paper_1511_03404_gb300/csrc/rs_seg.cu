@@ -11,9 +11,10 @@ namespace rs {
 
 namespace {
 
-template <class K, int VB, int R, int THREADS, int ITEMS, int CHUNK_TILES>
+template <class K, int VB, int R, int THREADS, int ITEMS, int CHUNK_TILES, int UNIT,
+          int SMALL_ITEMS>
 struct SegSort {
-  using C = SegKernelCfg<K, VB, R, THREADS, ITEMS, CHUNK_TILES>;
+  using C = SegKernelCfg<K, VB, R, THREADS, ITEMS, CHUNK_TILES, UNIT, SMALL_ITEMS>;
   static constexpr int PLAN_THREADS = 1024;
 
   static SegLayout layout(size_t n, size_t nseg, int passes) {
@@ -30,18 +31,18 @@ struct SegSort {
     cudaError_t e = cudaMemsetAsync(w, 0, L.memset_bytes, s);
     if (e != cudaSuccess) return e;
     k_seg_plan<PLAN_THREADS><<<1, PLAN_THREADS, 0, s>>>(
-        d_off, nseg, n, uint32_t(C::TILE), uint32_t(C::TILE), uint32_t(C::CHUNK), ctrl,
+        d_off, nseg, n, uint32_t(C::SMALL_TILE), uint32_t(C::TILE), uint32_t(C::CHUNK), ctrl,
         reinterpret_cast<uint32_t*>(w + L.small_ids), reinterpret_cast<SegDesc*>(w + L.descs),
         reinterpret_cast<uint32_t*>(w + L.tile_seg), reinterpret_cast<uint32_t*>(w + L.chunk_seg),
         L.tiles_max, L.chunks_max);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // short segments: one CTA each, before the persistent kernel
-    auto small = &k_seg_small<K, VB, R, THREADS, ITEMS>;
+    auto small = &k_seg_small<K, VB, R, THREADS, SMALL_ITEMS>;
     using SS = typename C::SS;
     const int occ_small = prepare_kernel(reinterpret_cast<const void*>(small), THREADS, SS::BYTES);
     if (occ_small <= 0) return cudaErrorInvalidConfiguration;
-    auto kern = &k_seg_persistent<K, VB, R, THREADS, ITEMS, CHUNK_TILES>;
+    auto kern = &k_seg_persistent<K, VB, R, THREADS, ITEMS, CHUNK_TILES, UNIT>;
     const int occ = prepare_kernel(reinterpret_cast<const void*>(kern), THREADS, C::BYTES);
     if (occ <= 0) return cudaErrorInvalidConfiguration;
     SegArgs a;
@@ -77,7 +78,9 @@ struct SegSort {
   }
 };
 
-using SegU32Pairs = SegSort<uint32_t, 4, 8, 256, 16, 8>;
+// pass tiles of 256 x 17 keys ranked in half-warp units; short segments up
+// to 4096 elements sorted whole by one CTA
+using SegU32Pairs = SegSort<uint32_t, 4, 8, 256, 17, 8, 16, 16>;
 
 }  // namespace
 

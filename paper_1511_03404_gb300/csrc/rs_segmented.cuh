@@ -176,17 +176,22 @@ struct SegSmallSmem {
   static constexpr int BYTES = VALS + (VB > 0 ? TILE * VB : 0);
 };
 
-template <class K, int VB, int RADIX_BITS, int THREADS, int ITEMS, int CHUNK_TILES>
+// UNIT: lanes per ranking unit of the pass tiles (32 or 16, as for the
+// onesweep pass); SMALL_ITEMS: keys per thread of the short-segment sort,
+// whose tile bounds a short segment.
+template <class K, int VB, int RADIX_BITS, int THREADS, int ITEMS, int CHUNK_TILES, int UNIT = 32,
+          int SMALL_ITEMS = ITEMS>
 struct SegKernelCfg {
   static constexpr int RADIX = 1 << RADIX_BITS;
   static constexpr int TILE = THREADS * ITEMS;
+  static constexpr int SMALL_TILE = THREADS * SMALL_ITEMS;
   static constexpr int CHUNK = TILE * CHUNK_TILES;
   static constexpr int MAXP = (8 * int(sizeof(K)) + RADIX_BITS - 1) / RADIX_BITS;
   // histogram counters: [pass][digit pair][16 slots], two 16-bit counts per word
   static constexpr int HIST_SLOTS = 16;
   static constexpr int HIST_BYTES = MAXP * (RADIX / 2) * HIST_SLOTS * 4;
-  using OS = OnesweepSmem<K, VB, RADIX_BITS, THREADS, ITEMS>;
-  using SS = SegSmallSmem<K, VB, RADIX_BITS, THREADS, ITEMS>;
+  using OS = OnesweepSmem<K, VB, RADIX_BITS, THREADS, ITEMS, UNIT>;
+  using SS = SegSmallSmem<K, VB, RADIX_BITS, THREADS, SMALL_ITEMS>;
   static constexpr int A = OS::BYTES;
   static constexpr int BODY = A > HIST_BYTES ? A : HIST_BYTES;
   static constexpr int MISC = (BODY + 15) / 16 * 16;  // u32 [8]
@@ -307,12 +312,12 @@ __global__ void __launch_bounds__(THREADS, 4)
   }
 }
 
-template <class K, int VB, int RADIX_BITS, int THREADS, int ITEMS, int CHUNK_TILES>
+template <class K, int VB, int RADIX_BITS, int THREADS, int ITEMS, int CHUNK_TILES, int UNIT = 32>
 __global__ void __launch_bounds__(THREADS, 4)
     k_seg_persistent(K* __restrict__ k0, ValT<VB>* __restrict__ v0, K* __restrict__ k1,
                      ValT<VB>* __restrict__ v1, SegArgs a) {
   using V = ValT<VB>;
-  using C = SegKernelCfg<K, VB, RADIX_BITS, THREADS, ITEMS, CHUNK_TILES>;
+  using C = SegKernelCfg<K, VB, RADIX_BITS, THREADS, ITEMS, CHUNK_TILES, UNIT>;
   constexpr int RADIX = C::RADIX, HALF = RADIX / 2, TILE = C::TILE, CHUNK = C::CHUNK;
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t* s_misc = reinterpret_cast<uint32_t*>(smem + C::MISC);
@@ -466,8 +471,8 @@ __global__ void __launch_bounds__(THREADS, 4)
         t.xf = KeyXf<K>{};
         t.xin = false;
         t.xout = false;
-        onesweep_tile<K, VB, RADIX_BITS, THREADS, ITEMS, true>(t, ctrl, a.knobs.timeout_ns,
-                                                               smem);
+        onesweep_tile<K, VB, RADIX_BITS, THREADS, ITEMS, true, false, UNIT>(
+            t, ctrl, a.knobs.timeout_ns, smem);
       }
       __syncthreads();
       if (tid == 0) {

@@ -388,6 +388,9 @@ struct OnesweepSmem {
   static constexpr int TILE = THREADS * ITEMS;
   static constexpr int ELEM = (int(sizeof(K)) > VB) ? int(sizeof(K)) : VB;
   static constexpr int WH = 0;                              // u32 [UNITS][RADIX] unit counters
+  // half-warp units: the counters are cleared by a bulk copy with each tile's keys
+  static constexpr uint32_t ZERO_BYTES = UNIT == 16 ? uint32_t(UNITS * RADIX * 4) : 0u;
+  static_assert(ZERO_BYTES <= 4096 * 4 && ZERO_BYTES % 16 == 0, "one bulk copy of zeros");
   static constexpr int CNT = WH + UNITS * RADIX * 4;       // u32 [RADIX] tile counts
   static constexpr int TSTART = CNT + RADIX * 4;           // u32 [RADIX] tile digit starts
   static constexpr int GBASE = TSTART + RADIX * 4;         // u32 [RADIX] global base
@@ -609,12 +612,22 @@ struct Stage {
   }
 };
 
+// Zeros in global memory, the source of the bulk copies that clear the rank
+// counters of a tile (one copy per TU; never written).
+namespace {
+__device__ __align__(128) uint32_t g_zero_words[4096];
+}
+
 // Start staging the keys of tile `tile` of an array of n keys into the key
 // buffer: one bulk copy issued by thread 0 on `bar`, head/tail elements and
-// the past-the-end sentinels written by every thread.
+// the past-the-end sentinels written by every thread.  zero_dst (optional):
+// zero_bytes (a multiple of 16, at most 16 KB) of shared memory cleared by a
+// second bulk copy on the same barrier, so that the tile's counters are zero
+// once its keys have landed, without a store loop on the shared-memory pipe.
 template <class K, int THREADS, int TILE, bool CG>
 __device__ __forceinline__ void stage_keys(unsigned char* kin, const K* ksrc, uint32_t n,
-                                           uint32_t tile, uint64_t* bar) {
+                                           uint32_t tile, uint64_t* bar,
+                                           void* zero_dst = nullptr, uint32_t zero_bytes = 0u) {
   const uint32_t tile_base = tile * uint32_t(TILE);
   const uint32_t tile_len = min(uint32_t(TILE), n - tile_base);
   const K* gk = ksrc + tile_base;
@@ -626,8 +639,9 @@ __device__ __forceinline__ void stage_keys(unsigned char* kin, const K* ksrc, ui
     // copy engine reads them
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if constexpr (CG) asm volatile("fence.proxy.async.global;" ::: "memory");
-    mbar_arrive_expect_tx(bar, sk.body);
+    mbar_arrive_expect_tx(bar, sk.body + zero_bytes);
     sk.issue(kin, gk, bar);
+    if (zero_bytes) bulk_load(zero_dst, g_zero_words, zero_bytes, bar);
   }
   sk.edges(kin, gk, tile_len);
   // past the end: the largest digit, so these items rank after every key of
@@ -688,8 +702,9 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
       if constexpr (VB > 0) mbar_init(&s_bar[1]);
     }
     __syncthreads();
-    // ---- stage the tile's keys
-    stage_keys<K, THREADS, TILE, CG>(smem + S::KIN, t.ksrc, n, tile, &s_bar[0]);
+    // ---- stage the tile's keys (half-warp units: and clear the counters)
+    stage_keys<K, THREADS, TILE, CG>(smem + S::KIN, t.ksrc, n, tile, &s_bar[0],
+                                     smem + S::WH, S::ZERO_BYTES);
   }
   if (tid == 0) s_misc[1] = 0u;
   K* s_kin = Stage<K>(t.ksrc + tile_base, tile_len).at(smem + S::KIN);
@@ -698,9 +713,7 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
       s_wh[i] = 0u;
       s_mm[i] = 0u;
     }
-  } else {
-    for (int i = tid; i < UNITS * RADIX; i += THREADS) s_wh[i] = 0u;
-  }
+  }  // half-warp units: the bulk copy that staged the keys cleared the counters
   bool landed = mbar_wait_bounded(&s_bar[0], parity, ctrl, timeout_ns, tile);
   if (!landed) landed = mbar_wait_bounded(&s_bar[0], parity, ctrl, timeout_ns, tile);
   if (__syncthreads_or(!landed)) {  // CTA-uniform
@@ -914,7 +927,9 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
       s_misc[4] = nxt < pf->tiles ? 1u : 0u;
     }
     __syncthreads();
-    if (s_misc[4]) stage_keys<K, THREADS, TILE, CG>(smem + S::KIN, t.ksrc, n, s_misc[3], &s_bar[0]);
+    if (s_misc[4])
+      stage_keys<K, THREADS, TILE, CG>(smem + S::KIN, t.ksrc, n, s_misc[3], &s_bar[0],
+                                       smem + S::WH, S::ZERO_BYTES);
   }
 
   // ---- scatter: consecutive threads take consecutive stage slots, which map
@@ -975,7 +990,8 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
       __syncthreads();
       if constexpr (PERSIST) {
         if (s_misc[4])
-          stage_keys<K, THREADS, TILE, CG>(smem + S::KIN, t.ksrc, n, s_misc[3], &s_bar[0]);
+          stage_keys<K, THREADS, TILE, CG>(smem + S::KIN, t.ksrc, n, s_misc[3], &s_bar[0],
+                                           smem + S::WH, S::ZERO_BYTES);
       }
       if (full) {
 #pragma unroll
@@ -1100,7 +1116,8 @@ __global__ void __launch_bounds__(THREADS, MINB)
   t.xout = xf.on && pass == 31 - __clz(exec);
   uint32_t tile = s_misc[3];
   if (tile < tiles && s_misc[2] == 0u)
-    stage_keys<K, THREADS, S::TILE, false>(smem + S::KIN, t.ksrc, n, tile, &s_bar[0]);
+    stage_keys<K, THREADS, S::TILE, false>(smem + S::KIN, t.ksrc, n, tile, &s_bar[0],
+                                           smem + S::WH, S::ZERO_BYTES);
   else
     tile = tiles;  // nothing to do
   if (threadIdx.x == 0) s_misc[4] = 0u;

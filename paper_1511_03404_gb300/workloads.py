@@ -11,6 +11,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import os
 import statistics
 import sys
 
@@ -22,6 +23,9 @@ _L2_FLUSH_BYTES = 256 << 20
 
 
 def _uniform_u32(n: int, seed: int = 1):
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    if root not in sys.path:  # the seeded generators live beside the package
+        sys.path.insert(0, root)
     import inputs  # seeded generators shared with the tests; no sort arithmetic
     return inputs.keys(np.uint32, "uniform", n, seed=seed)
 

@@ -151,10 +151,21 @@ def cpu_oracle_rate(sample_n: int, dists=DISTS, budget_s: float = 12.0) -> dict:
         used.append(d)
         if t_total > budget_s:
             break
+    # a library stable sort beside it on the same arrays (numpy: one thread)
+    t_lib = 0.0
+    for d in used:
+        k = inputs.keys(np.uint32, d, sample_n)
+        t0 = time.perf_counter()
+        order = np.argsort(k, kind="stable")
+        k[order], vals[order]  # the sorted pairs
+        t_lib += time.perf_counter() - t0
     return {"value": done / t_total / 1e9, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
             "sample": f"{len(used)} arrays of 2^{int(np.log2(sample_n))} u32 pairs "
                       f"({', '.join(used)}), single-threaded C LSD counting sort, "
-                      f"{t_total:.1f} s"}
+                      f"{t_total:.1f} s",
+            "library_stable_sort": {"value": done / t_lib / 1e9, "unit": "Gkeys/s", "cores": 1,
+                                    "what": "numpy.argsort(kind='stable') and the gather of keys "
+                                            "and values, same arrays"}}
 
 
 def max_over_ranks(x: float, dist, device) -> float:

@@ -105,3 +105,18 @@ def test_host_argument_checks_without_gpu():
                                 None) == (rs.RS_OK, 0)
     assert rs.rs_debug_set(99, 1) == rs.RS_ERR_INVALID
     assert rs.rs_profile_end()[0] == rs.RS_ERR_INVALID
+
+
+def test_server_entry_points_reject_null_without_gpu():
+    """The server's query and policy entry points check their arguments on
+    the host: a NULL server or output is RS_ERR_INVALID, nothing is touched."""
+    lib = rs.load()
+    import ctypes
+    out = ctypes.c_size_t()
+    cfg = rs.rs_server_config(1 << 14, 1 << 22, 1 << 21, 2, 1)
+    assert lib.rs_server_get_config(None, ctypes.byref(cfg)) == rs.RS_ERR_INVALID
+    assert lib.rs_server_set_config(None, ctypes.byref(cfg)) == rs.RS_ERR_INVALID
+    assert lib.rs_server_trace(None, None, 0, ctypes.byref(out)) == rs.RS_ERR_INVALID
+    assert lib.rs_server_completed(None, None, 0, ctypes.byref(out)) == rs.RS_ERR_INVALID
+    assert lib.rs_server_stats(None, None) == rs.RS_ERR_INVALID
+    assert lib.rs_poll(None, 1, None) == rs.RS_ERR_INVALID

@@ -162,6 +162,20 @@ __device__ __forceinline__ void report_error(Ctrl* ctrl, uint32_t code, uint32_t
   if (atomicCAS(&ctrl->error, 0u, code) == 0u) atomicExch(&ctrl->error_info, info);
 }
 
+// Programmatic dependent launch.  A kernel launched with programmatic stream
+// serialization may start while the kernel before it on the stream is still
+// running; pdl_wait() blocks (in hardware) until that kernel has completed and
+// its memory operations are visible, and is a no-op for an ordinary launch.
+// pdl_launch_dependents() lets the next such kernel be scheduled once every
+// CTA of this grid has called it or exited.
+__device__ __forceinline__ void pdl_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+__device__ __forceinline__ void pdl_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
   uint32_t v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -264,6 +278,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   extern __shared__ uint32_t sh[];  // [passes][RADIX][SLOTS]
   __shared__ uint32_t s_tot[32];
   __shared__ int s_last;
+  pdl_launch_dependents();  // the first pass may be scheduled beside this grid
 
   const int tid = threadIdx.x, lane = tid & 31;
   const uint32_t slot = uint32_t(lane & (SLOTS - 1));
@@ -1030,6 +1045,8 @@ __global__ void __launch_bounds__(THREADS, MINB)
   using S = OnesweepSmem<K, VB, RADIX_BITS, THREADS, ITEMS, UNIT>;
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t* s_misc = reinterpret_cast<uint32_t*>(smem + S::MISC);
+  pdl_wait();  // the kernel before (upsweep or previous pass) is complete
+  pdl_launch_dependents();
 
   const uint32_t exec = ctrl->exec_mask;
   if (!((exec >> pass) & 1u)) return;  // every key has the same digit: nothing moves
@@ -1084,6 +1101,8 @@ __global__ void __launch_bounds__(THREADS, MINB)
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t* s_misc = reinterpret_cast<uint32_t*>(smem + S::MISC);
   uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem + S::MBAR);
+  pdl_wait();  // the kernel before (upsweep or previous pass) is complete
+  pdl_launch_dependents();
 
   const uint32_t exec = ctrl->exec_mask;
   if (!((exec >> pass) & 1u)) return;  // every key has the same digit: nothing moves

@@ -86,15 +86,31 @@ struct OnesweepSort {
       const int width = std::min(R, a.end_bit - lo);
       const uint32_t mask = (1u << width) - 1u;
       prof_before(a.stream);
-      kern<<<grid, THREADS, S::BYTES, a.stream>>>(
-          static_cast<K*>(a.keys), static_cast<K*>(a.keys_alt), static_cast<V*>(a.vals),
-          static_cast<V*>(a.vals_alt), a.n, p, uint32_t(lo), mask,
-          reinterpret_cast<const uint32_t*>(ws + L.offsets) + size_t(p) * RADIX,
+      // programmatic dependent launch: the pass's CTAs may be scheduled while
+      // the kernel before it finishes; each waits for it (pdl_wait) first.
+      // Only for grids that fill the GPU (resident CTAs, or more tiles than
+      // slots): a one-wave grid scheduled early lands unevenly on the SMs
+      // that happen to have room, and measured slower.
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(grid);
+      cfg.blockDim = dim3(THREADS);
+      cfg.dynamicSmemBytes = S::BYTES;
+      cfg.stream = a.stream;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      attr[0].val.programmaticStreamSerializationAllowed = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = (PERSIST || nt > size_t(device_info().sms) * occ) ? 1 : 0;
+      e = cudaLaunchKernelEx(
+          &cfg, kern, static_cast<K*>(a.keys), static_cast<K*>(a.keys_alt),
+          static_cast<V*>(a.vals), static_cast<V*>(a.vals_alt), a.n, p, uint32_t(lo), mask,
+          static_cast<const uint32_t*>(reinterpret_cast<const uint32_t*>(ws + L.offsets) +
+                                       size_t(p) * RADIX),
           reinterpret_cast<uint32_t*>(ws + L.status) + size_t(p) * L.tiles * RADIX,
           reinterpret_cast<uint32_t*>(ws + L.gagg) + size_t(p) * L.groups * RADIX,
           reinterpret_cast<uint32_t*>(ws + L.ginc) + size_t(p) * L.groups * RADIX, uint32_t(nt),
           ctrl, a.knobs, xf);
-      e = cudaGetLastError();
+      if (e == cudaSuccess) e = cudaGetLastError();
       prof_after(a.stream, 1, bytes, slot, p);
       if (e != cudaSuccess) return e;
     }

@@ -108,6 +108,23 @@ def test_unaligned_buffers(dtype, pairs):
             check_case(dtype, pairs, "uniform", n, offset_elems=off)
 
 
+@pytest.mark.parametrize("dtype,pairs", TYPES, ids=TYPE_IDS)
+def test_unaligned_buffers_every_multi_cta_variant(dtype, pairs):
+    """Every one-CTA-per-tile and resident-CTA variant (warp and half-warp
+    ranking units) on buffers 1-3 elements past a 16-byte boundary, over
+    several tiles and a ragged tail: the bulk copies start at the aligned
+    part and the head and tail elements are loaded by threads."""
+    kb = np.dtype(dtype).itemsize
+    vb = kb if pairs else 0
+    for var in variants(kb, vb):
+        if var["kind"] not in (0, 2):
+            continue
+        tile = var["threads"] * var["items"]
+        for off in (1, 3):
+            check_case(dtype, pairs, "uniform", 3 * tile + 5, offset_elems=off,
+                       variant=var["index"])
+
+
 def test_non_default_stream():
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):

@@ -350,10 +350,13 @@ rs_status rs_segmented_workspace_bytes(size_t n, size_t n_seg, int begin_bit, in
  * current at creation.  A scheduler thread admits queued requests, oldest
  * first, whenever the request's device footprint fits the free part of the
  * pool and a stream is free; a request that does not fit yet does not block
- * younger ones that do.  Admitted 32-bit pair requests of at most 2^14
- * elements (same bit range) are packed into one batched segmented sort;
- * every other request runs as its own sort.  Each admitted unit runs
- * copy-in, sort, copy-out on its stream, so units overlap on the device.
+ * younger ones that do.  Admitted 32-bit pair requests of at most
+ * batch_max_n elements (same bit range; 2^14 by default, see
+ * rs_server_config) are packed into one batched segmented sort, which takes
+ * a free stream before any single request does; every other request runs as
+ * its own sort, large ones (large_n elements and up) at most max_large at a
+ * time.  Each admitted unit runs copy-in, sort, copy-out on its stream, so
+ * units overlap on the device.
  * The sorted result of a request does not depend on what it was batched or
  * overlapped with.
  */

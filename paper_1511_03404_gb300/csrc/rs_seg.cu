@@ -42,6 +42,11 @@ struct SegSort {
     using SS = typename C::SS;
     const int occ_small = prepare_kernel(reinterpret_cast<const void*>(small), THREADS, SS::BYTES);
     if (occ_small <= 0) return cudaErrorInvalidConfiguration;
+    auto hist = &k_seg_hist<K, R, C::HIST_THREADS, C::MAXP, C::HIST_SLOTS, C::CHUNK, C::TILE,
+                            CHUNK_TILES>;
+    const int occ_hist =
+        prepare_kernel(reinterpret_cast<const void*>(hist), C::HIST_THREADS, C::HIST_BYTES);
+    if (occ_hist <= 0) return cudaErrorInvalidConfiguration;
     auto kern = &k_seg_persistent<K, VB, R, THREADS, ITEMS, CHUNK_TILES, UNIT>;
     const int occ = prepare_kernel(reinterpret_cast<const void*>(kern), THREADS, C::BYTES);
     if (occ <= 0) return cudaErrorInvalidConfiguration;
@@ -69,6 +74,8 @@ struct SegSort {
     small<<<grid_small, THREADS, SS::BYTES, s>>>(static_cast<K*>(keys), static_cast<V*>(vals),
                                                  static_cast<K*>(keys_alt),
                                                  static_cast<V*>(vals_alt), a);
+    hist<<<unsigned(device_info().sms * occ_hist), C::HIST_THREADS,
+           passes * C::RADIX * C::HIST_SLOTS * 4, s>>>(static_cast<const K*>(keys), a);
     kern<<<grid, THREADS, C::BYTES, s>>>(static_cast<K*>(keys), static_cast<V*>(vals),
                                          static_cast<K*>(keys_alt), static_cast<V*>(vals_alt), a);
     e = cudaGetLastError();
@@ -80,7 +87,7 @@ struct SegSort {
 
 // pass tiles of 256 x 17 keys ranked in half-warp units; short segments up
 // to 4096 elements sorted whole by one CTA
-using SegU32Pairs = SegSort<uint32_t, 4, 8, 256, 17, 8, 16, 16>;
+using SegU32Pairs = SegSort<uint32_t, 4, 8, 256, 17, 32, 16, 16>;
 
 }  // namespace
 

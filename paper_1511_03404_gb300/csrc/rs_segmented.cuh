@@ -187,14 +187,13 @@ struct SegKernelCfg {
   static constexpr int SMALL_TILE = THREADS * SMALL_ITEMS;
   static constexpr int CHUNK = TILE * CHUNK_TILES;
   static constexpr int MAXP = (8 * int(sizeof(K)) + RADIX_BITS - 1) / RADIX_BITS;
-  // histogram counters: [pass][digit pair][16 slots], two 16-bit counts per word
+  // histogram kernel: [pass][digit][16 lane slots] u32 counters, 1024 threads
+  static constexpr int HIST_THREADS = 1024;
   static constexpr int HIST_SLOTS = 16;
-  static constexpr int HIST_BYTES = MAXP * (RADIX / 2) * HIST_SLOTS * 4;
+  static constexpr int HIST_BYTES = MAXP * RADIX * HIST_SLOTS * 4;
   using OS = OnesweepSmem<K, VB, RADIX_BITS, THREADS, ITEMS, UNIT>;
   using SS = SegSmallSmem<K, VB, RADIX_BITS, THREADS, SMALL_ITEMS>;
-  static constexpr int A = OS::BYTES;
-  static constexpr int BODY = A > HIST_BYTES ? A : HIST_BYTES;
-  static constexpr int MISC = (BODY + 15) / 16 * 16;  // u32 [8]
+  static constexpr int MISC = (OS::BYTES + 15) / 16 * 16;  // u32 [8]
   static constexpr int BYTES = MISC + 32;
 };
 
@@ -312,23 +311,135 @@ __global__ void __launch_bounds__(THREADS, 4)
   }
 }
 
+// Digit histograms of the long segments, every pass (Sec. 2.6, the counting
+// step), one chunk of CHUNK keys at a time, grid-stride over the chunks.  As in
+// the whole-array upsweep: 16-byte loads, every pass's digit counted into
+// per-lane-slot shared counters, then the chunk's counts added to its
+// segment's.  The chunk also clears the look-back words of its tiles.  The
+// last chunk of a segment (ticket) scans the segment's histograms, chooses the
+// passes that move data and marks the segment ready for its pass tiles.
+template <class K, int RADIX_BITS, int THREADS, int MAXP, int SLOTS, int CHUNK, int TILE,
+          int CHUNK_TILES>
+__global__ void __launch_bounds__(THREADS, 2)
+    k_seg_hist(const K* __restrict__ k0, SegArgs a) {
+  constexpr int RADIX = 1 << RADIX_BITS;
+  constexpr int VEC = 16 / int(sizeof(K));
+  static_assert(RADIX <= THREADS, "one thread per digit in the scan");
+  extern __shared__ uint32_t sh[];  // [passes][RADIX][SLOTS]
+  __shared__ uint32_t s_tot[32];
+  __shared__ int s_last;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const uint32_t slot = uint32_t(lane & (SLOTS - 1));
+  const int passes = a.passes;
+  uint32_t shiftp[MAXP], maskp[MAXP];
+#pragma unroll
+  for (int p = 0; p < MAXP; ++p) {
+    const int lo = a.begin_bit + p * RADIX_BITS;
+    const int hi = min(lo + RADIX_BITS, a.end_bit);
+    shiftp[p] = p < passes ? uint32_t(lo) : 0u;
+    maskp[p] = p < passes ? ((1u << (hi - lo)) - 1u) : 0u;
+  }
+  auto count_key = [&](K k) {
+#pragma unroll
+    for (int p = 0; p < MAXP; ++p)
+      if (p < passes)
+        atomicAdd(&sh[(p * RADIX + int(digit_of(k, shiftp[p], maskp[p]))) * SLOTS + int(slot)],
+                  1u);
+  };
+  const uint32_t n_chunks = a.ctrl->tile_counter[kNChunks];
+  const int words = passes * RADIX * SLOTS;
+  for (uint32_t item = blockIdx.x; item < n_chunks; item += gridDim.x) {
+    const uint32_t li = a.chunk_seg[item];
+    const SegDesc d = a.descs[li];
+    const uint32_t lc = item - d.chunk0;
+    const uint32_t start = lc * uint32_t(CHUNK);
+    const uint32_t len = min(uint32_t(CHUNK), d.len - start);
+    const K* keys = k0 + d.off + start;
+    for (int i = tid; i < words; i += THREADS) sh[i] = 0u;
+    __syncthreads();
+    // 16-byte aligned body, scalar head and tail
+    const uintptr_t addr = reinterpret_cast<uintptr_t>(keys);
+    uint32_t head = uint32_t(((16u - (addr & 15u)) & 15u) / sizeof(K));
+    if (head > len) head = len;
+    const uint32_t nvec = (len - head) / VEC;
+    const uint32_t tail = head + nvec * VEC;
+    if (uint32_t(tid) < head) count_key(keys[tid]);
+    if (uint32_t(tid) < len - tail) count_key(keys[tail + tid]);
+    const uint4* vp = reinterpret_cast<const uint4*>(keys + head);
+    for (uint32_t i = tid; i < nvec; i += THREADS) {
+      const uint4 v = vp[i];
+      const K* ks = reinterpret_cast<const K*>(&v);
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) count_key(ks[e]);
+    }
+    __syncthreads();
+    // the chunk's counts into the segment's: one (pass, digit) per thread
+    uint32_t* cnt = a.counts + size_t(li) * passes * RADIX;
+    for (int w = tid; w < passes * RADIX; w += THREADS) {
+      const uint32_t* row = sh + w * SLOTS;
+      uint32_t c = 0u;
+#pragma unroll
+      for (int l = 0; l < SLOTS; ++l) c += row[(l + lane) & (SLOTS - 1)];  // rotated: no conflicts
+      if (c) atomicAdd(&cnt[w], c);
+    }
+    // clear the look-back words of this chunk's tiles, every pass
+    const uint32_t t_first = lc * uint32_t(CHUNK_TILES);
+    const uint32_t t_last = min(t_first + uint32_t(CHUNK_TILES), (d.len + TILE - 1) / TILE);
+    for (int p = 0; p < passes; ++p) {
+      uint32_t* st = a.status + size_t(p) * a.tiles_max * RADIX;
+      const uint32_t nw = (t_last - t_first) * RADIX;
+      for (uint32_t i = tid; i < nw; i += THREADS)
+        st[lb_index<RADIX>(d.tile0 + t_first + i / RADIX, i % RADIX)] = 0u;
+    }
+    __syncthreads();
+    uint32_t* state = a.state + size_t(li) * kSegStateWords;
+    if (tid == 0) {
+      // the CTA's counts and cleared words (ordered before by the barrier)
+      // become visible before the ticket
+      __threadfence();
+      const uint32_t chunks = (d.len + CHUNK - 1) / CHUNK;
+      s_last = atomicAdd(&state[kSegTicket], 1u) == chunks - 1u;
+    }
+    __syncthreads();
+    if (s_last) {
+      // last chunk of the segment: scan each pass's histogram
+      __threadfence();
+      uint32_t* offs = a.offsets + size_t(li) * passes * RADIX;
+      uint32_t exec = 0u;
+      for (int p = 0; p < passes; ++p) {
+        const uint32_t c = tid < RADIX ? ld_relaxed(&cnt[p * RADIX + tid]) : 0u;
+        const uint32_t e = block_exclusive_scan<THREADS>(c, s_tot);
+        if (tid < RADIX) offs[p * RADIX + tid] = e;
+        if (!__syncthreads_or(tid < RADIX && c == d.len)) exec |= 1u << p;
+      }
+      if (tid == 0) {
+        if ((__popc(exec) & 1) != (passes & 1)) {
+          const uint32_t skipped = ~exec & ((1u << passes) - 1u);
+          exec |= skipped & (0u - skipped);
+        }
+        __threadfence();
+        st_release(&state[kSegReady], 1u | (exec << 1));
+      }
+    }
+    __syncthreads();
+  }
+}
+
 template <class K, int VB, int RADIX_BITS, int THREADS, int ITEMS, int CHUNK_TILES, int UNIT = 32>
 __global__ void __launch_bounds__(THREADS, 4)
     k_seg_persistent(K* __restrict__ k0, ValT<VB>* __restrict__ v0, K* __restrict__ k1,
                      ValT<VB>* __restrict__ v1, SegArgs a) {
   using V = ValT<VB>;
   using C = SegKernelCfg<K, VB, RADIX_BITS, THREADS, ITEMS, CHUNK_TILES, UNIT>;
-  constexpr int RADIX = C::RADIX, HALF = RADIX / 2, TILE = C::TILE, CHUNK = C::CHUNK;
+  constexpr int RADIX = C::RADIX, TILE = C::TILE;
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t* s_misc = reinterpret_cast<uint32_t*>(smem + C::MISC);
-  const int tid = threadIdx.x, lane = tid & 31;
+  const int tid = threadIdx.x;
   Ctrl* ctrl = a.ctrl;
   const int passes = a.passes;
 
   const uint32_t n_tiles = ctrl->tile_counter[kNTiles];
-  const uint32_t n_chunks = ctrl->tile_counter[kNChunks];
-  const uint32_t q_pass = n_chunks;
-  const uint32_t q_end = q_pass + uint32_t(passes) * n_tiles;
+  const uint32_t q_end = uint32_t(passes) * n_tiles;
 
   for (;;) {
     if (tid == 0) {
@@ -339,146 +450,68 @@ __global__ void __launch_bounds__(THREADS, 4)
     const uint32_t item = s_misc[0];
     if (item >= q_end || s_misc[1] != 0u) break;  // CTA-uniform
 
-    if (item < q_pass) {
-      // ---- digit histograms of one chunk of a long segment, every pass
-      const uint32_t li = a.chunk_seg[item];
-      const SegDesc d = a.descs[li];
-      const uint32_t lc = item - d.chunk0;
-      const uint32_t start = lc * uint32_t(CHUNK);
-      const uint32_t len = min(uint32_t(CHUNK), d.len - start);
-      const K* keys = k0 + d.off + start;
-      uint32_t* sh = reinterpret_cast<uint32_t*>(smem);
-      constexpr int SL = C::HIST_SLOTS;
-      const int slot = lane & (SL - 1);
-      for (int i = tid; i < passes * HALF * SL; i += THREADS) sh[i] = 0u;
-      __syncthreads();
-      for (uint32_t i = tid; i < len; i += THREADS) {
-        const K k = keys[i];
-        for (int p = 0; p < passes; ++p) {
-          const int lo = a.begin_bit + p * RADIX_BITS;
-          const uint32_t m = (1u << (min(lo + RADIX_BITS, a.end_bit) - lo)) - 1u;
-          const uint32_t dg = digit_of(k, uint32_t(lo), m);
-          atomicAdd(&sh[(p * HALF + int(dg >> 1)) * SL + slot], 1u << ((dg & 1u) << 4));
-        }
+    // ---- one tile of one pass of a long segment
+    const int p = int(item / n_tiles);
+    const uint32_t gt = item - uint32_t(p) * n_tiles;
+    const uint32_t li = a.tile_seg[gt];
+    const SegDesc d = a.descs[li];
+    uint32_t* state = a.state + size_t(li) * kSegStateWords;
+    const uint32_t ntiles = (d.len + TILE - 1) / TILE;
+    if (tid == 0) {
+      // both conditions read at once (one round trip); the bounded waits
+      // only when one of them does not hold yet
+      uint32_t ready = ld_relaxed(&state[kSegReady]);
+      const uint32_t done = p > 0 ? ld_relaxed(&state[kSegDone0 + p - 1]) : ntiles;
+      bool ok = (ready & 1u) && done >= ntiles;
+      if (ok) {
+        __threadfence();  // acquire: the histograms and the previous pass's output
+      } else {
+        ok = wait_geq(&state[kSegReady], 1u, ctrl, a.knobs.timeout_ns, gt);
+        if (ok && p > 0) ok = wait_geq(&state[kSegDone0 + p - 1], ntiles, ctrl,
+                                       a.knobs.timeout_ns, gt);
+        ready = ld_acquire(&state[kSegReady]);
       }
-      __syncthreads();
-      uint32_t* cnt = a.counts + size_t(li) * passes * RADIX;
-      for (int w = tid; w < passes * HALF; w += THREADS) {
-        uint32_t lo = 0u, hi = 0u;
-        const uint32_t* row = sh + w * SL;
-        for (int l = 0; l < SL; ++l) {
-          const uint32_t x = row[(l + slot) & (SL - 1)];
-          lo += x & 0xFFFFu;
-          hi += x >> 16;
-        }
-        const int p = w / HALF, dg = (w - p * HALF) * 2;
-        if (lo) atomicAdd(&cnt[p * RADIX + dg], lo);
-        if (hi) atomicAdd(&cnt[p * RADIX + dg + 1], hi);
+      s_misc[3] = ok ? 1u : 0u;
+      s_misc[4] = ready >> 1;
+    }
+    __syncthreads();
+    const uint32_t exec = s_misc[4];
+    if (s_misc[3] && ((exec >> p) & 1u)) {
+      const bool from_alt = (__popc(exec & ((1u << p) - 1u)) & 1) != 0;
+      TileArgs<K, VB> t;
+      t.ksrc = (from_alt ? k1 : k0) + d.off;
+      t.kdst = (from_alt ? k0 : k1) + d.off;
+      if constexpr (VB > 0) {
+        t.vsrc = (from_alt ? v1 : v0) + d.off;
+        t.vdst = (from_alt ? v0 : v1) + d.off;
+      } else {
+        t.vsrc = nullptr;
+        t.vdst = nullptr;
       }
-      // clear the look-back words of this chunk's tiles, every pass
-      const uint32_t t_first = lc * uint32_t(CHUNK_TILES);
-      const uint32_t t_last = min(t_first + uint32_t(CHUNK_TILES), (d.len + TILE - 1) / TILE);
-      for (int p = 0; p < passes; ++p) {
-        uint32_t* st = a.status + size_t(p) * a.tiles_max * RADIX;
-        const uint32_t words = (t_last - t_first) * RADIX;
-        for (uint32_t i = tid; i < words; i += THREADS)
-          st[lb_index<RADIX>(d.tile0 + t_first + i / RADIX, i % RADIX)] = 0u;
-      }
-      __syncthreads();
-      uint32_t* state = a.state + size_t(li) * kSegStateWords;
-      if (tid == 0) {
-        // the CTA's counts and cleared words (ordered before by the barrier)
-        // become visible before the ticket
-        __threadfence();
-        const uint32_t chunks = (d.len + CHUNK - 1) / CHUNK;
-        s_misc[2] = atomicAdd(&state[kSegTicket], 1u) == chunks - 1u;
-      }
-      __syncthreads();
-      if (s_misc[2]) {
-        // last chunk of the segment: scan each pass's histogram
-        __threadfence();
-        uint32_t* offs = a.offsets + size_t(li) * passes * RADIX;
-        uint32_t exec = 0u;
-        for (int p = 0; p < passes; ++p) {
-          const uint32_t c = tid < RADIX ? ld_relaxed(&cnt[p * RADIX + tid]) : 0u;
-          const uint32_t e = block_exclusive_scan<THREADS>(c, reinterpret_cast<uint32_t*>(smem));
-          if (tid < RADIX) offs[p * RADIX + tid] = e;
-          if (!__syncthreads_or(tid < RADIX && c == d.len)) exec |= 1u << p;
-        }
-        if (tid == 0) {
-          if ((__popc(exec) & 1) != (passes & 1)) {
-            const uint32_t skipped = ~exec & ((1u << passes) - 1u);
-            exec |= skipped & (0u - skipped);
-          }
-          __threadfence();
-          st_release(&state[kSegReady], 1u | (exec << 1));
-        }
-      }
-    } else {
-      // ---- one tile of one pass of a long segment
-      const uint32_t q = item - q_pass;
-      const int p = int(q / n_tiles);
-      const uint32_t gt = q - uint32_t(p) * n_tiles;
-      const uint32_t li = a.tile_seg[gt];
-      const SegDesc d = a.descs[li];
-      uint32_t* state = a.state + size_t(li) * kSegStateWords;
-      const uint32_t ntiles = (d.len + TILE - 1) / TILE;
-      if (tid == 0) {
-        // both conditions read at once (one round trip); the bounded waits
-        // only when one of them does not hold yet
-        uint32_t ready = ld_relaxed(&state[kSegReady]);
-        const uint32_t done = p > 0 ? ld_relaxed(&state[kSegDone0 + p - 1]) : ntiles;
-        bool ok = (ready & 1u) && done >= ntiles;
-        if (ok) {
-          __threadfence();  // acquire: the histograms and the previous pass's output
-        } else {
-          ok = wait_geq(&state[kSegReady], 1u, ctrl, a.knobs.timeout_ns, gt);
-          if (ok && p > 0) ok = wait_geq(&state[kSegDone0 + p - 1], ntiles, ctrl,
-                                         a.knobs.timeout_ns, gt);
-          ready = ld_acquire(&state[kSegReady]);
-        }
-        s_misc[3] = ok ? 1u : 0u;
-        s_misc[4] = ready >> 1;
-      }
-      __syncthreads();
-      const uint32_t exec = s_misc[4];
-      if (s_misc[3] && ((exec >> p) & 1u)) {
-        const bool from_alt = (__popc(exec & ((1u << p) - 1u)) & 1) != 0;
-        TileArgs<K, VB> t;
-        t.ksrc = (from_alt ? k1 : k0) + d.off;
-        t.kdst = (from_alt ? k0 : k1) + d.off;
-        if constexpr (VB > 0) {
-          t.vsrc = (from_alt ? v1 : v0) + d.off;
-          t.vdst = (from_alt ? v0 : v1) + d.off;
-        } else {
-          t.vsrc = nullptr;
-          t.vdst = nullptr;
-        }
-        t.n = d.len;
-        t.tile = gt - d.tile0;
-        const int lo = a.begin_bit + p * RADIX_BITS;
-        t.shift = uint32_t(lo);
-        t.mask = (1u << (min(lo + RADIX_BITS, a.end_bit) - lo)) - 1u;
-        t.pass_offsets = a.offsets + (size_t(li) * passes + p) * RADIX;
-        t.status = a.status + size_t(p) * a.tiles_max * RADIX;
-        t.tile0 = d.tile0;
-        t.gagg = nullptr;  // segments are short: flat walk
-        t.ginc = nullptr;
-        t.tiles = ntiles;
-        t.silent = false;
-        t.trace = nullptr;
-        t.lb_small = false;
-        t.xf = KeyXf<K>{};
-        t.xin = false;
-        t.xout = false;
-        onesweep_tile<K, VB, RADIX_BITS, THREADS, ITEMS, true, false, UNIT>(
-            t, ctrl, a.knobs.timeout_ns, smem);
-      }
-      __syncthreads();
-      if (tid == 0) {
-        __threadfence();  // the tile's output, ordered before by the barrier, then the count
-        atomicAdd(&state[kSegDone0 + p], 1u);
-      }
+      t.n = d.len;
+      t.tile = gt - d.tile0;
+      const int lo = a.begin_bit + p * RADIX_BITS;
+      t.shift = uint32_t(lo);
+      t.mask = (1u << (min(lo + RADIX_BITS, a.end_bit) - lo)) - 1u;
+      t.pass_offsets = a.offsets + (size_t(li) * passes + p) * RADIX;
+      t.status = a.status + size_t(p) * a.tiles_max * RADIX;
+      t.tile0 = d.tile0;
+      t.gagg = nullptr;  // segments are short: flat walk
+      t.ginc = nullptr;
+      t.tiles = ntiles;
+      t.silent = false;
+      t.trace = nullptr;
+      t.lb_small = false;
+      t.xf = KeyXf<K>{};
+      t.xin = false;
+      t.xout = false;
+      onesweep_tile<K, VB, RADIX_BITS, THREADS, ITEMS, true, false, UNIT>(
+          t, ctrl, a.knobs.timeout_ns, smem);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();  // the tile's output, ordered before by the barrier, then the count
+      atomicAdd(&state[kSegDone0 + p], 1u);
     }
     __syncthreads();
   }

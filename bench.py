@@ -696,7 +696,7 @@ def bench_segmented(torch, rs, dev, scaled: bool, reps: int = 3) -> dict:
            "batched_ms": b_ms, "batched_gkeys_s": n / (b_ms / 1e3) / 1e9,
            "plain_ms": plain_ms, "plain_gkeys_s": n / (plain_ms / 1e3) / 1e9,
            "batched_over_plain": plain_ms / b_ms,
-           "batched": "one CUDA graph replay: memset + planning kernel + short-segment kernel + one persistent kernel",
+           "batched": "one CUDA graph replay: memset + planning kernel + short-segment kernel + histogram kernel + one persistent kernel",
            "plain": "one rs_sort_pairs_u32 call per segment on the same stream"}
     del pk, pv, k, v, ka, va, ws, wsp
     torch.cuda.empty_cache()

@@ -319,8 +319,10 @@ rs_status rs_workspace_status(const void* ws, rs_stream_t stream, uint32_t* info
 
 /*
  * Batched segmented sort of 32-bit key-value pairs: the sort of Sec. 2.6
- * applied independently to every segment of one array, all segments in one
- * persistent kernel launch (after a one-CTA planning launch).
+ * applied independently to every segment of one array, in a fixed sequence of
+ * launches whatever the segments: a one-CTA planning launch, one kernel for the
+ * short segments, one for the long segments' histograms and one persistent
+ * kernel for all their passes.
  *   keys, vals, keys_alt, vals_alt  [n] u32 device buffers as for rs_sort_pairs_u32
  *   d_offsets  [n_seg + 1] u64 device: segment s is [d_offsets[s], d_offsets[s+1]);
  *              d_offsets[0] = 0, non-decreasing, d_offsets[n_seg] = n, and no

@@ -1,6 +1,7 @@
 // Host side of the batched segmented sort (32-bit key-value pairs):
 // workspace sizing and the launch sequence memset -> k_seg_plan ->
-// k_seg_persistent, all on the caller's stream (capturable in a CUDA graph).
+// k_seg_small -> k_seg_hist -> k_seg_persistent, all on the caller's stream
+// (capturable in a CUDA graph).
 #include <algorithm>
 
 #include "../../include/rs.h"

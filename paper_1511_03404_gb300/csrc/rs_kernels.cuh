@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     k_upsweep(const K* __restrict__ keys, uint32_t n, int begin_bit, int end_bit, int passes,
               uint32_t* __restrict__ counts, uint32_t* __restrict__ offsets,
               Ctrl* __restrict__ ctrl, uint4* __restrict__ zero_base, uint64_t zero_vec4,
-              KeyXf<K> xf) {
+              KeyXf<K> xf, bool early_dependents) {
   constexpr int RADIX = 1 << RADIX_BITS;
   constexpr int SLOTS = sizeof(K) == 4 ? 32 : 16;
   constexpr int VEC = 16 / int(sizeof(K));
@@ -278,7 +278,9 @@ __global__ void __launch_bounds__(THREADS, 1)
   extern __shared__ uint32_t sh[];  // [passes][RADIX][SLOTS]
   __shared__ uint32_t s_tot[32];
   __shared__ int s_last;
-  pdl_launch_dependents();  // the first pass may be scheduled beside this grid
+  // a first pass that fills the GPU may be scheduled beside this grid (one
+  // that does not is scheduled as this grid's CTAs exit)
+  if (early_dependents) pdl_launch_dependents();
 
   const int tid = threadIdx.x, lane = tid & 31;
   const uint32_t slot = uint32_t(lane & (SLOTS - 1));
@@ -1041,12 +1043,15 @@ __global__ void __launch_bounds__(THREADS, MINB)
                ValT<VB>* __restrict__ v1, uint32_t n, int pass, uint32_t shift, uint32_t mask,
                const uint32_t* __restrict__ pass_offsets, uint32_t* __restrict__ status,
                uint32_t* __restrict__ gagg, uint32_t* __restrict__ ginc, uint32_t tiles,
-               Ctrl* __restrict__ ctrl, Knobs knobs, KeyXf<K> xf) {
+               Ctrl* __restrict__ ctrl, Knobs knobs, KeyXf<K> xf, bool early_dependents) {
   using S = OnesweepSmem<K, VB, RADIX_BITS, THREADS, ITEMS, UNIT>;
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t* s_misc = reinterpret_cast<uint32_t*>(smem + S::MISC);
   pdl_wait();  // the kernel before (upsweep or previous pass) is complete
-  pdl_launch_dependents();
+  // a grid of more tiles than CTA slots lets the next pass be scheduled
+  // during its last wave; a one-wave grid lets it in as its CTAs exit, so
+  // that the next pass's CTAs spread over the SMs
+  if (early_dependents) pdl_launch_dependents();
 
   const uint32_t exec = ctrl->exec_mask;
   if (!((exec >> pass) & 1u)) return;  // every key has the same digit: nothing moves
@@ -1096,13 +1101,13 @@ __global__ void __launch_bounds__(THREADS, MINB)
                        uint32_t mask, const uint32_t* __restrict__ pass_offsets,
                        uint32_t* __restrict__ status, uint32_t* __restrict__ gagg,
                        uint32_t* __restrict__ ginc, uint32_t tiles, Ctrl* __restrict__ ctrl,
-                       Knobs knobs, KeyXf<K> xf) {
+                       Knobs knobs, KeyXf<K> xf, bool early_dependents) {
   using S = OnesweepSmem<K, VB, RADIX_BITS, THREADS, ITEMS, UNIT>;
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t* s_misc = reinterpret_cast<uint32_t*>(smem + S::MISC);
   uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem + S::MBAR);
   pdl_wait();  // the kernel before (upsweep or previous pass) is complete
-  pdl_launch_dependents();
+  if (early_dependents) pdl_launch_dependents();
 
   const uint32_t exec = ctrl->exec_mask;
   if (!((exec >> pass) & 1u)) return;  // every key has the same digit: nothing moves

@@ -31,7 +31,10 @@ struct OnesweepSort {
     return onesweep_layout(passes, R, tiles(n)).total;
   }
 
-  static cudaError_t upsweep(const SortArgs& a, int passes, const Layout& L, bool clear_status) {
+  // early: the kernel after this one (the first pass) may be scheduled as
+  // soon as this one starts, because its grid fills the GPU anyway
+  static cudaError_t upsweep(const SortArgs& a, int passes, const Layout& L, bool clear_status,
+                             bool early = false) {
     char* ws = static_cast<char*>(a.ws);
     Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws);
     cudaError_t e = cudaMemsetAsync(ws, 0, L.memset_bytes, a.stream);
@@ -54,7 +57,7 @@ struct OnesweepSort {
         static_cast<const K*>(a.keys), a.n, a.begin_bit, a.end_bit, passes,
         reinterpret_cast<uint32_t*>(ws + L.counts), reinterpret_cast<uint32_t*>(ws + L.offsets),
         ctrl, reinterpret_cast<uint4*>(ws + L.status), zero_vec4,
-        make_key_xf<K>(a.key_kind, a.descending));
+        make_key_xf<K>(a.key_kind, a.descending), early);
     e = cudaGetLastError();
     prof_after(a.stream, 0, double(a.n) * sizeof(K));
     return e;
@@ -65,11 +68,6 @@ struct OnesweepSort {
     *in_alt = passes & 1;
     const size_t nt = tiles(a.n);
     const Layout L = onesweep_layout(passes, R, nt);
-    cudaError_t e = upsweep(a, passes, L, true);
-    if (e != cudaSuccess) return e;
-    char* ws = static_cast<char*>(a.ws);
-    Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws);
-    const int slot = prof_note_mask(a.stream, &ctrl->exec_mask);
     using V = ValT<VB>;
     auto kern = [] {  // instantiate only the kernel this variant launches
       if constexpr (PERSIST) return &k_onesweep_persist<K, VB, R, THREADS, ITEMS, MINB, UNIT>;
@@ -77,6 +75,16 @@ struct OnesweepSort {
     }();
     const int occ = prepare_kernel(reinterpret_cast<const void*>(kern), THREADS, S::BYTES);
     if (occ <= 0) return cudaErrorInvalidConfiguration;
+    // a pass grid that fills the GPU (resident CTAs, or more tiles than CTA
+    // slots) is scheduled early, while the kernel before it runs; a one-wave
+    // grid scheduled that early lands on whichever SMs have room, so it is
+    // let in only as the kernel before it exits
+    const bool fills = PERSIST || nt > size_t(device_info().sms) * occ;
+    cudaError_t e = upsweep(a, passes, L, true, fills);
+    if (e != cudaSuccess) return e;
+    char* ws = static_cast<char*>(a.ws);
+    Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws);
+    const int slot = prof_note_mask(a.stream, &ctrl->exec_mask);
     const unsigned grid =
         PERSIST ? unsigned(std::min<size_t>(nt, size_t(device_info().sms) * occ)) : unsigned(nt);
     const double bytes = 2.0 * double(a.n) * double(sizeof(K) + VB);
@@ -86,11 +94,9 @@ struct OnesweepSort {
       const int width = std::min(R, a.end_bit - lo);
       const uint32_t mask = (1u << width) - 1u;
       prof_before(a.stream);
-      // programmatic dependent launch: the pass's CTAs may be scheduled while
-      // the kernel before it finishes; each waits for it (pdl_wait) first.
-      // Only for grids that fill the GPU (resident CTAs, or more tiles than
-      // slots): a one-wave grid scheduled early lands unevenly on the SMs
-      // that happen to have room, and measured slower.
+      // programmatic dependent launch: the pass's CTAs may be scheduled before
+      // the kernel ahead of it has finished (when that one lets them in);
+      // each waits for it (pdl_wait) first, so the launch gap is hidden
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3(grid);
       cfg.blockDim = dim3(THREADS);
@@ -100,7 +106,7 @@ struct OnesweepSort {
       attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
       attr[0].val.programmaticStreamSerializationAllowed = 1;
       cfg.attrs = attr;
-      cfg.numAttrs = (PERSIST || nt > size_t(device_info().sms) * occ) ? 1 : 0;
+      cfg.numAttrs = 1;
       e = cudaLaunchKernelEx(
           &cfg, kern, static_cast<K*>(a.keys), static_cast<K*>(a.keys_alt),
           static_cast<V*>(a.vals), static_cast<V*>(a.vals_alt), a.n, p, uint32_t(lo), mask,
@@ -109,7 +115,7 @@ struct OnesweepSort {
           reinterpret_cast<uint32_t*>(ws + L.status) + size_t(p) * L.tiles * RADIX,
           reinterpret_cast<uint32_t*>(ws + L.gagg) + size_t(p) * L.groups * RADIX,
           reinterpret_cast<uint32_t*>(ws + L.ginc) + size_t(p) * L.groups * RADIX, uint32_t(nt),
-          ctrl, a.knobs, xf);
+          ctrl, a.knobs, xf, fills);
       if (e == cudaSuccess) e = cudaGetLastError();
       prof_after(a.stream, 1, bytes, slot, p);
       if (e != cudaSuccess) return e;

@@ -353,6 +353,7 @@ def run_ours(args):
         "cpu_baseline": None,
         "e2e": {"value": e2e["value"], "unit": "Gkeys/s",
                 "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
+                "runs": e2e.get("runs_gkeys_per_s"),
                 "serial": e2e.get("serial"), "link_bound": e2e.get("link_bound"),
                 "pipelining": e2e.get("pipelining")},
         "gpu_launches": launches,
@@ -498,9 +499,13 @@ def e2e_rate(torch, rs, keys_h, vals_h, n, dev, ws, args, dists) -> dict:
     timed(1, 2)
     ms_serial = timed(1, max(4, steps // 2))
     timed(nsets, nsets)
-    ms = timed(nsets, steps)
+    # the pipelined run three times, the median reported: on these hosts a
+    # single run now and then loses its copy overlap (the sort is unchanged)
+    ms_runs = [timed(nsets, steps) for _ in range(3)]
+    ms = statistics.median(ms_runs)
     link = min(link_ms() for _ in range(3))
     return {"value": n / (ms / 1e3) / 1e9, "ms_per_step": ms, "h2d": 2 * 4 * n, "d2h": 2 * 4 * n,
+            "runs_gkeys_per_s": [n / (m / 1e3) / 1e9 for m in ms_runs],
             "serial": {"value": n / (ms_serial / 1e3) / 1e9, "ms_per_step": ms_serial},
             "link_bound": {"value": n / (link / 1e3) / 1e9, "ms_per_step": link,
                            "what": "the step's host->device and device->host bytes copied at once, "

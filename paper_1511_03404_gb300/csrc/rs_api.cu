@@ -3,6 +3,7 @@
 // event timing and the test-only fault-injection knobs.
 #include <algorithm>
 #include <atomic>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -79,6 +80,11 @@ static std::atomic<long long> g_trace_ptr{0};
 static std::atomic<long long> g_trace_tiles{0};
 static std::atomic<long long> g_trace_pass{0};
 static std::atomic<long long> g_lb_small{0};
+
+bool pdl_enabled() {
+  static const bool on = std::getenv("RS_NO_PDL") == nullptr;
+  return on;
+}
 
 Knobs knobs_now() {
   Knobs k;

@@ -58,6 +58,10 @@ const DeviceInfo& device_info();
 // (once per device) and return its resident CTAs per SM at `threads`.
 int prepare_kernel(const void* func, int threads, int smem_bytes);
 
+// Whether digit passes use programmatic dependent launch (on unless the
+// environment sets RS_NO_PDL, read once; a diagnostic switch).
+bool pdl_enabled();
+
 // Per-kernel timing hooks (no-ops unless rs_profile_begin was called on this thread).
 // A onesweep launch only moves data when its pass bit is set in the
 // workspace's exec mask; prof_note_mask copies that mask to the host (only

@@ -79,7 +79,8 @@ struct OnesweepSort {
     // slots) is scheduled early, while the kernel before it runs; a one-wave
     // grid scheduled that early lands on whichever SMs have room, so it is
     // let in only as the kernel before it exits
-    const bool fills = PERSIST || nt > size_t(device_info().sms) * occ;
+    const bool pdl = pdl_enabled();
+    const bool fills = pdl && (PERSIST || nt > size_t(device_info().sms) * occ);
     cudaError_t e = upsweep(a, passes, L, true, fills);
     if (e != cudaSuccess) return e;
     char* ws = static_cast<char*>(a.ws);
@@ -106,7 +107,7 @@ struct OnesweepSort {
       attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
       attr[0].val.programmaticStreamSerializationAllowed = 1;
       cfg.attrs = attr;
-      cfg.numAttrs = 1;
+      cfg.numAttrs = pdl ? 1 : 0;
       e = cudaLaunchKernelEx(
           &cfg, kern, static_cast<K*>(a.keys), static_cast<K*>(a.keys_alt),
           static_cast<V*>(a.vals), static_cast<V*>(a.vals_alt), a.n, p, uint32_t(lo), mask,

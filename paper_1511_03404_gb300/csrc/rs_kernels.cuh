@@ -6,7 +6,8 @@
 //               takes the exclusive scan of each histogram (the "prefix"
 //               step) and decides which passes move data.
 //   k_onesweep  one digit pass: the tile's keys are ranked within the tile
-//               (stable: warp-major, then item, then lane order), the tile's
+//               (stable: ranking-unit-major, a unit being a warp or half a
+//               warp, then item, then lane order), the tile's
 //               digit counts are published for the following tiles, the
 //               tile's global digit offsets come from a decoupled look-back
 //               over the preceding tiles, and the tile is scattered through

@@ -418,8 +418,8 @@ struct OnesweepSmem {
   // the tile's keys as loaded (+16 B skew); once they are staged in OUT, the
   // tile's values are loaded here
   static constexpr int KIN = (MBAR + 16 + 15) / 16 * 16;
-  // the tile in (digit, input) order: keys, then values; during the rank it
-  // holds the warps' peer masks (u32 [WARPS][RADIX])
+  // the tile in (digit, input) order: keys, then values; during the rank of
+  // warp units it holds the warps' peer masks (u32 [WARPS][RADIX])
   static constexpr int OUT = KIN + TILE * ELEM + 16;
   static constexpr int MM = OUT;
   static constexpr int OUT_BYTES =
@@ -771,7 +771,7 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
   stamp(t.trace, 2);
 
   // ---- per digit: tile count, publish it; then the exclusive prefix over
-  // warps, which starts at the digit's first slot in the tile
+  // the ranking units, which starts at the digit's first slot in the tile
   uint32_t my_cnt = 0u;
   constexpr int CSHIFT = UNIT == 32 ? 0 : 16;  // where the unit counters keep the count
   if (tid < RADIX) {

@@ -282,3 +282,26 @@ def test_lookback_wait_is_bounded():
         rs.rs_debug_set(rs.RS_DEBUG_TIMEOUT_NS, 1_000_000_000)
     # the same context sorts correctly afterwards
     check_case(np.uint32, False, "uniform", 2**20)
+
+
+def test_without_dependent_launch_same_result():
+    """With RS_NO_PDL set (read once per process) the passes are launched the
+    ordinary way; the sorted output is the same."""
+    import subprocess
+    import sys
+    import os
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = (
+        "import sys; sys.path.insert(0, %r); sys.path.insert(0, %r)\n"
+        "import numpy as np, inputs, oracle, torch\n"
+        "from gpu_util import sort_via_abi\n"
+        "for n in (5 * 4352 + 3, 1 << 21, (1 << 23) + 5):\n"
+        "    k = inputs.keys(np.uint32, 'uniform', n); v = inputs.values(np.uint32, n)\n"
+        "    gk, gv, _ = sort_via_abi(torch, k, v)\n"
+        "    ek, ev = oracle.lsd_sort(k, v)\n"
+        "    assert np.array_equal(gk, ek) and np.array_equal(gv, ev)\n"
+        "print('ok')\n" % (root, os.path.join(root, "tests")))
+    env = dict(os.environ, RS_NO_PDL="1")
+    res = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                         timeout=600)
+    assert res.returncode == 0 and res.stdout.strip().endswith("ok"), res.stderr[-2000:]

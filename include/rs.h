@@ -411,7 +411,7 @@ typedef struct rs_server_config {
   size_t batch_max_n;    /* u32 pair requests of 2..batch_max_n elements are batched [2^14] */
   size_t max_batch_keys; /* elements per batched launch at most, >= batch_max_n [2^22] */
   size_t large_n;        /* requests of at least large_n elements are "large" [2^21] */
-  int max_large;         /* large units admitted at once, oldest first, 1..64 [2] */
+  int max_large;         /* large units admitted at once, oldest first, 1..64 [3] */
   int large_low_priority; /* 1: large units run on low-priority streams, so that the
                              kernels of short requests are scheduled ahead of them [1] */
 } rs_server_config;

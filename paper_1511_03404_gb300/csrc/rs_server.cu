@@ -109,7 +109,7 @@ struct rs_server {
   // between them and stretches every one (the tail of the latency), while
   // shorter requests keep the other streams.
   size_t large_n = size_t(1) << 21;
-  int max_large = 2;
+  int max_large = 3;
   int large_low_priority = 1;
   int large_running = 0;
   std::mutex mu;

@@ -178,7 +178,7 @@ def test_config_policies_same_results():
         st, cfg = rs.rs_server_get_config(srv)
         rs.check(st)
         assert cfg == {"batch_max_n": 1 << 14, "max_batch_keys": 1 << 22, "large_n": 1 << 21,
-                       "max_large": 2, "large_low_priority": 1}
+                       "max_large": 3, "large_low_priority": 1}
         for bad in ({"batch_max_n": 1 << 23}, {"max_batch_keys": (1 << 30) + 1},
                     {"large_n": 0}, {"max_large": 0}, {"max_large": 65},
                     {"large_low_priority": 2}):

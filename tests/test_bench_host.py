@@ -86,3 +86,19 @@ def test_clock_summary_parsing():
     s = c.summary()
     assert s["sm_mhz"] == 2010 and s["sm_max_mhz"] == 2070 and s["samples"] == 3
     assert s["reasons"] == ["sw_power_cap"]
+
+
+def test_kernel_source_hash_ignores_comments(tmp_path, monkeypatch):
+    """The DRAM-traffic figure is keyed by a hash of the pass's code: comments
+    and blank lines do not change it, code does."""
+    csrc = tmp_path / "paper_1511_03404_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    for name in bench.ONESWEEP_SOURCES:
+        (csrc / name).write_text("int a = 1;  // one\n\nint b = 2;\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h0 = bench.kernel_source_hash()
+    first = csrc / bench.ONESWEEP_SOURCES[0]
+    first.write_text("// a new comment\nint a = 1;  // changed comment\nint b = 2;\n\n")
+    assert bench.kernel_source_hash() == h0
+    first.write_text("int a = 3;\nint b = 2;\n")
+    assert bench.kernel_source_hash() != h0

@@ -1,5 +1,6 @@
 """Named, timed workloads of the library's other entry points: merge sort
-(Sec. 2.4) and the sample-sort partition (Sec. 2.7) on seeded uniform keys.
+(Sec. 2.4), the sample-sort partition (Sec. 2.7) and the batched segmented
+sort, on seeded uniform keys.
 
 Each function runs its entry point on the device, times it with CUDA events
 on the launching stream (the input restored outside the events, L2 flushed
@@ -147,9 +148,50 @@ def sample_partition(n: int = 1 << 26, samples: int = 64, buckets: int = 64, rep
             "bytes": "block sort: 2 n (4 + 4); bucket counts: 4 n; run copy: 2 n (4 + 4)"}
 
 
+def segmented(n: int = 1 << 24, nseg: int = 1000, reps: int = 5, peak_gbs=None,
+              device: int = 0) -> dict:
+    """Batched segmented sort of u32 pairs (values = index): nseg segments of
+    log-uniform lengths in [1, 2^20] (seed 1) scaled to n elements in all,
+    through ``rs_segmented_sort_pairs``."""
+    import torch
+    _uniform_u32(1)  # puts the input generators on the path
+    import inputs
+    dev = torch.device("cuda", device)
+    stream = torch.cuda.Stream(dev)
+    lengths = inputs.scale_lengths(inputs.segment_lengths(nseg, seed=1, max_log2=20), n)
+    off = inputs.offsets_from_lengths(lengths)
+    total = int(off[-1])
+    keys0 = torch.from_numpy(_uniform_u32(total).view(np.int32)).to(dev)
+    vals0 = torch.arange(total, dtype=torch.int32, device=dev)
+    k, v = torch.empty_like(keys0), torch.empty_like(keys0)
+    ka, va = torch.empty_like(keys0), torch.empty_like(keys0)
+    doff = torch.from_numpy(off.view(np.int64)).to(dev)
+    st, need = rs.rs_segmented_workspace_bytes(total, len(lengths), 0, 32)
+    rs.check(st, "rs_segmented_workspace_bytes")
+    ws = torch.empty(max(need, 256), dtype=torch.uint8, device=dev)
+
+    def restore():
+        with torch.cuda.stream(stream):
+            k.copy_(keys0)
+            v.copy_(vals0)
+
+    def call():
+        st_, _ = rs.rs_segmented_sort_pairs(k.data_ptr(), v.data_ptr(), ka.data_ptr(),
+                                            va.data_ptr(), total, doff.data_ptr(), len(lengths),
+                                            0, 32, ws.data_ptr(), ws.numel(), stream.cuda_stream)
+        rs.check(st_, "rs_segmented_sort_pairs")
+
+    ms, prof = _timed(torch, stream, restore, call, reps)
+    return {"workload": f"segmented sort, u32 pairs, {len(lengths)} log-uniform segments scaled "
+                        f"to n={total}, uniform keys (mt19937 seed 1)",
+            "ms": ms, "gkeys_per_s": total / (ms / 1e3) / 1e9,
+            "kernels": _kernel_rate(prof["segmented"], peak_gbs),
+            "bytes": "histograms 4 n, then 2 n (4 + 4) per pass"}
+
+
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser(description="run one named workload and print its timing")
-    ap.add_argument("workload", choices=("merge", "merge_pairs", "sample_partition"))
+    ap.add_argument("workload", choices=("merge", "merge_pairs", "sample_partition", "segmented"))
     ap.add_argument("--n", type=int, default=1 << 26)
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--buckets", type=int, default=64)
@@ -159,6 +201,8 @@ def main(argv=None) -> int:
         r = merge(args.n, 4, 0, args.reps)
     elif args.workload == "merge_pairs":
         r = merge(args.n, 4, 4, args.reps)
+    elif args.workload == "segmented":
+        r = segmented(args.n, 1000, args.reps)
     else:
         r = sample_partition(args.n, args.buckets, args.buckets, args.reps)
     print(json.dumps(r))

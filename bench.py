@@ -50,8 +50,7 @@ L2_FLUSH_BYTES = 256 << 20
 # and traffic is null.
 NCU_TRAFFIC = {
     "78ff4f2bdf27cac7": {"bytes_per_launch": 1103401728, "n": 1 << 26,
-                         "kernel": "k_onesweep_persist<u32,4,8,256,17,4,16>",
-                         "summary": "profiles/traffic_onesweep_kv32_2p26.md"},
+                         "kernel": "k_onesweep_persist<u32,4,8,256,17,4,16>"},
 }
 
 ONESWEEP_SOURCES = ("rs_kernels.cuh", "rs_common.h", "rs_launch.cuh", "rs_inst_kv32.cu")
@@ -342,6 +341,8 @@ def run_ours(args):
         traffic = t["bytes_per_launch"]
     line = {
         "metric": METRIC, "value": value, "unit": "Gkeys/s", "n_gpus": world,
+        "value_by_distribution": {d: n / (statistics.mean(step_ms[i::len(dists)]) / 1e3) / 1e9
+                                  for i, d in enumerate(dists) if step_ms[i::len(dists)]},
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic",
@@ -366,7 +367,7 @@ def run_ours(args):
                 "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
                 "runs": e2e.get("runs_gkeys_per_s"),
                 "serial": e2e.get("serial"), "link_bound": e2e.get("link_bound"),
-                "pipelining": e2e.get("pipelining")},
+                "entry": e2e.get("entry"), "pipelining": e2e.get("pipelining")},
         "gpu_launches": launches,
         "clocks": clocks.summary(),
         "kernel_source": src,
@@ -391,10 +392,49 @@ def run_ours(args):
         stage("cpu baseline (oracle)")
         line["cpu_baseline"] = cpu_oracle_rate(n)
         line["cpu_baseline"]["host"] = host_description()
+    line["summary"] = summary(line)
+    stage("summary " + json.dumps(line["summary"]))
     print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()
     return 0
+
+
+def summary(line: dict) -> dict:
+    """The headline figures of every leg in a few hundred bytes, the last key
+    of the bench line (and the last stderr line), so that a reader who keeps
+    only the end of the output still has them."""
+    r = lambda x, d=2: None if x is None else round(float(x), d)  # noqa: E731
+    out = {"gkeys_per_s": r(line["value"]),
+           "uniform_gkeys_per_s": r(line["value_by_distribution"].get("uniform")),
+           "onesweep_frac_of_hbm": r(line["roofline"]["frac"], 3),
+           "e2e_gkeys_per_s": r(line["e2e"]["value"])}
+    u64 = line.get("u64_2p27")
+    if u64:
+        out["u64_2p27_gkeys_per_s"] = {d: [r(u64[d]["keys_gkeys_per_s"]),
+                                           r(u64[d]["pairs_gkeys_per_s"])]
+                                       for d in ("uniform", "gaussian", "entropy16") if d in u64}
+    seg = line.get("segmented")
+    if seg:
+        out["segmented"] = {"elements": seg["elements"], "batched_gkeys_per_s":
+                            r(seg["batched_gkeys_s"]), "plain_gkeys_per_s": r(seg["plain_gkeys_s"]),
+                            "batched_over_plain": r(seg["batched_over_plain"])}
+    srv = line.get("serving")
+    if srv:
+        svp = srv.get("served_vs_plain", {})
+        out["serving"] = {"p50_ms": r(srv["p50_ms"]), "p99_ms": r(srv["p99_ms"]),
+                          "gkeys_per_s": r(srv["gkeys_per_s"]),
+                          "offered_gkeys_per_s": r(srv["offered_gkeys_per_s"]),
+                          "saturated_gkeys_per_s": r(svp.get("served_gkeys_per_s")),
+                          "plain_gkeys_per_s": r(svp.get("plain_gkeys_per_s")),
+                          "served_over_plain": r(svp.get("served_over_plain"))}
+    small = line.get("u32_keys_2p20")
+    if small:
+        out["u32_keys_2p20_ms"] = r(small.get("ms_per_call", small.get("ms")), 4)
+    cpu = line.get("cpu_baseline")
+    if cpu:
+        out["cpu_oracle_gkeys_per_s"] = r(cpu["value"], 4)
+    return out
 
 
 def host_description() -> str:
@@ -423,13 +463,42 @@ def check_sorted(torch, k_out, v_out, k_in) -> bool:
     return bool((idx[1:][eq] > idx[:-1][eq]).all())
 
 
-def e2e_rate(torch, rs, keys_h, vals_h, n, dev, ws, args, dists) -> dict:
-    """Host -> device copy, sort, device -> host copy, per step, through the C ABI.
+def check_segmented(torch, src, out_k, out_v, off) -> bool:
+    """Every segment sorted stably, checked on the device.  The values are
+    the input positions, so these properties fix the result: keys
+    non-decreasing inside each segment; the values a permutation of 0 .. n-1
+    with every value inside its own position's segment; src[value] equal to
+    the output key; equal keys of a segment in increasing value order."""
+    n = src.numel()
+    dev = src.device
+    lengths = torch.from_numpy(np.diff(off).astype(np.int64)).to(dev)
+    seg = torch.repeat_interleave(torch.arange(lengths.numel(), dtype=torch.int32, device=dev),
+                                  lengths, output_size=n)
+    same = seg[1:] == seg[:-1]
+    o = out_k ^ -(1 << 31)  # unsigned order as signed order
+    if not bool(((o[1:] >= o[:-1]) | ~same).all()):
+        return False
+    idx = out_v.long()
+    if int(idx.min()) != 0 or int(idx.max()) != n - 1:
+        return False
+    seen = torch.zeros(n, dtype=torch.uint8, device=dev)
+    seen[idx] = 1
+    ok = bool(seen.bool().all())
+    del seen
+    ok = ok and bool((seg[idx] == seg).all()) and bool((src[idx] == out_k).all())
+    eq = (o[1:] == o[:-1]) & same
+    return ok and bool(((idx[1:] > idx[:-1]) | ~eq).all())
 
-    Three streams form a pipeline over three sets of device buffers and pinned
-    host outputs: the copy-in stream loads step i + 1 while the sort stream
-    sorts step i and the copy-out stream returns step i - 1; events order each
-    set's reuse.  ``serial`` is the same with one buffer set (no overlap), and
+
+def e2e_rate(torch, rs, keys_h, vals_h, n, dev, ws, args, dists) -> dict:
+    """Host -> device copy, sort, device -> host copy, per step, through the
+    C ABI's host-buffer entry point rs_sort_host (one call per step does all
+    three on its stream).
+
+    Steps go round robin over three streams, each with its own device buffers
+    and pinned host outputs, so the copy-in of step i + 1, the sort of step i
+    and the copy-out of step i - 1 overlap (stream order keeps each buffer
+    set's reuse in order).  ``serial`` is one stream (no overlap), and
     ``link_bound`` the step time the host link alone allows (both directions
     at once, measured here)."""
     hk = {d: torch.from_numpy(keys_h[d].view(np.int32)).pin_memory() for d in dists}
@@ -444,43 +513,27 @@ def e2e_rate(torch, rs, keys_h, vals_h, n, dev, ws, args, dists) -> dict:
             "ov": torch.empty(n, dtype=torch.int32).pin_memory(),
             "ws": ws if j == 0 else torch.empty_like(ws),
         })
-    s_in, s_sort, s_out = (torch.cuda.Stream(dev) for _ in range(3))
+    streams = [torch.cuda.Stream(dev) for _ in range(nsets)]
+    s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)  # the link-bound probe
 
     def timed(nb, steps):
-        free = [None] * nb  # per set: the event after its last copy-out
         torch.cuda.synchronize()
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
-        t0.record(s_in)
-        s_sort.wait_event(t0)
-        s_out.wait_event(t0)
+        t0.record(streams[0])
+        for s in streams[1:nb]:
+            s.wait_event(t0)
         for i in range(steps):
             d = dists[i % len(dists)]
-            sl = sets[i % nb]
-            if free[i % nb] is not None:
-                s_in.wait_event(free[i % nb])
-            with torch.cuda.stream(s_in):
-                sl["k"].copy_(hk[d], non_blocking=True)
-                sl["v"].copy_(hv, non_blocking=True)
-            loaded = torch.cuda.Event()
-            loaded.record(s_in)
-            s_sort.wait_event(loaded)
-            st, in_alt = rs.rs_sort_pairs_u32(sl["k"].data_ptr(), sl["v"].data_ptr(),
-                                              sl["ka"].data_ptr(), sl["va"].data_ptr(), n, 0, 32,
-                                              sl["ws"].data_ptr(), sl["ws"].numel(),
-                                              s_sort.cuda_stream)
-            rs.check(st, "rs_sort_pairs_u32")
-            sorted_ = torch.cuda.Event()
-            sorted_.record(s_sort)
-            s_out.wait_event(sorted_)
-            with torch.cuda.stream(s_out):
-                sl["ok"].copy_(sl["ka"] if in_alt else sl["k"], non_blocking=True)
-                sl["ov"].copy_(sl["va"] if in_alt else sl["v"], non_blocking=True)
-            free[i % nb] = torch.cuda.Event()
-            free[i % nb].record(s_out)
-        s_in.wait_stream(s_sort)
-        s_in.wait_stream(s_out)
-        t1.record(s_in)
+            sl, s = sets[i % nb], streams[i % nb]
+            st, _ = rs.rs_sort_host(4, 4, hk[d].data_ptr(), hv.data_ptr(), sl["ok"].data_ptr(),
+                                    sl["ov"].data_ptr(), n, 0, 32, sl["k"].data_ptr(),
+                                    sl["v"].data_ptr(), sl["ka"].data_ptr(), sl["va"].data_ptr(),
+                                    sl["ws"].data_ptr(), sl["ws"].numel(), s.cuda_stream)
+            rs.check(st, "rs_sort_host")
+        for s in streams[1:nb]:
+            streams[0].wait_stream(s)
+        t1.record(streams[0])
         torch.cuda.synchronize()
         # the last outputs are complete and sorted
         last = sets[(steps - 1) % nb]
@@ -521,8 +574,11 @@ def e2e_rate(torch, rs, keys_h, vals_h, n, dev, ws, args, dists) -> dict:
             "link_bound": {"value": n / (link / 1e3) / 1e9, "ms_per_step": link,
                            "what": "the step's host->device and device->host bytes copied at once, "
                                    "no sort"},
-            "pipelining": "three streams (copy-in, sort, copy-out) over three buffer sets: step "
-                          "i + 1 loads while step i sorts and step i - 1 returns; serial: one set"}
+            "entry": "rs_sort_host (C ABI: host->device copies, sort, device->host copies "
+                     "on one stream)",
+            "pipelining": "one rs_sort_host call per step, round robin over three streams and "
+                          "buffer sets: step i + 1 loads while step i sorts and step i - 1 "
+                          "returns; serial: one stream"}
 
 
 def _time_sorts(torch, rs, kb, vb, keys, vals, reps, stream):
@@ -676,15 +732,9 @@ def bench_segmented(torch, rs, dev, scaled: bool, reps: int = 3) -> dict:
         stream.synchronize()
         batched.append(e0.elapsed_time(e1))
     rs.check(rs.rs_workspace_status(ws.data_ptr(), h)[0], "segmented device status")
-    # spot check: 64 segments against numpy's sort of the same slice
-    out_k = (ka if in_alt else k)
-    rng = np.random.default_rng(0)
-    for s in rng.choice(len(lengths), 64, replace=False):
-        a, b = int(off[s]), int(off[s + 1])
-        got = out_k[a:b].cpu().numpy().view(np.uint32)
-        want = np.sort(pk[a:b].cpu().numpy().view(np.uint32))
-        if not np.array_equal(got, want):
-            raise SystemExit(f"bench: segment {s} not sorted correctly")
+    # the timed output, checked whole on the device (keys and values)
+    if not check_segmented(torch, pk, ka if in_alt else k, va if in_alt else v, off):
+        raise SystemExit("bench: the batched segmented sort failed its property check")
     # plain: one sort per segment through the typed entry point
     maxlen = int(lengths.max())
     st, need_p = rs.rs_workspace_bytes(4, 4, maxlen, 0, 32)
@@ -712,6 +762,9 @@ def bench_segmented(torch, rs, dev, scaled: bool, reps: int = 3) -> dict:
            "batched_ms": b_ms, "batched_gkeys_s": n / (b_ms / 1e3) / 1e9,
            "plain_ms": plain_ms, "plain_gkeys_s": n / (plain_ms / 1e3) / 1e9,
            "batched_over_plain": plain_ms / b_ms,
+           "checked": "the timed output, whole, on the device: keys sorted in every segment, "
+                      "values a permutation kept in their segments, keys follow their values, "
+                      "ties in input order",
            "batched": "one CUDA graph replay: memset + planning kernel + short-segment kernel + histogram kernel + one persistent kernel",
            "plain": "one rs_sort_pairs_u32 call per segment on the same stream"}
     del pk, pv, k, v, ka, va, ws, wsp
@@ -720,10 +773,17 @@ def bench_segmented(torch, rs, dev, scaled: bool, reps: int = 3) -> dict:
 
 
 def bench_serving(torch, rs, seconds: float = 10.0, rate: float = 5000.0,
-                  budget: int = 24 << 30, streams: int = 8) -> dict:
+                  budget: int = 24 << 30, streams: int = 8, compare_requests: int = 10000) -> dict:
     """Poisson arrivals at `rate` requests/s of log-uniform size [2^10, 2^24],
     half u32 pairs, half u64 keys (uniform keys), through the sort server
-    with a 24 GiB admission budget; p50/p99 latency and aggregate Gkeys/s."""
+    with a 24 GiB admission budget; p50/p99 latency and aggregate Gkeys/s.
+
+    Then the first `compare_requests` requests of the same trace twice more,
+    with no arrival schedule: ``saturated`` submits them all as fast as the
+    server admits them (its capacity: continuous batching, copies and sorts
+    of different requests overlapping on its streams), ``plain`` runs them one
+    after another as one rs_sort_host call each (copy in, sort, copy out) on
+    one stream, from and to the same pinned host buffers."""
     count = int(seconds * rate)
     raw = inputs.mt19937(1, 3 * count)
     u = raw.astype(np.float64) / 2.0**32
@@ -738,76 +798,127 @@ def bench_serving(torch, rs, seconds: float = 10.0, rate: float = 5000.0,
     ring = torch.empty(ring_bytes, dtype=torch.uint8).pin_memory()
     ring_base = ring.data_ptr()
     link_before = host_link_gbs(torch, ring)
-    st, srv = rs.rs_server_create(budget, streams)
-    rs.check(st, "rs_server_create")
-    pending = {}        # handle -> (ring start, ring end)
-    live = []           # ring regions in use, in allocation order
-    head = 0
-    reqs = []           # keep the ctypes structs alive
     offsets = (raw[0::3][:count].astype(np.int64) % (pool_n - (1 << 24)))
-
-    def reserve(nbytes):
-        nonlocal head
-        while True:
-            start = head if head + nbytes <= ring_bytes else 0
-            end = start + nbytes
-            if not any(a < end and start < b for a, b in live):
-                head = end
-                live.append((start, end))
-                return start
-            poll_some(block=True)
-
-    def poll_some(block=False):
-        # one call takes every finished handle off the server's completion
-        # queue; polling each pending handle instead kept the server's lock
-        # busy and starved its scheduler thread
-        st_, finished = rs.rs_server_completed(srv, 4096)
-        rs.check(st_, "rs_server_completed")
-        for hnd in finished:
-            st_, done = rs.rs_poll(srv, hnd)
-            if st_ != rs.RS_OK or not done:
-                raise SystemExit(f"bench: server request failed: {rs.status_string(st_)}")
-            live.remove(pending.pop(hnd))
-        if block and pending:
-            time.sleep(0.0002)
-
     arrival = np.cumsum(gaps)
-    # no cyclic garbage collection while the client keeps the arrival
-    # schedule: a full collection over a large heap stalls it for tens of ms
-    gc.collect()
-    gc.disable()
-    t0 = time.perf_counter()
-    for i in range(count):
-        while True:
-            rem = arrival[i] - (time.perf_counter() - t0)
-            if rem <= 0:
-                break
-            poll_some()
-            if rem > 3e-4:
-                time.sleep(1e-4)  # far from the next arrival: leave the lock alone
+
+    def request(i, out):
         n = int(sizes[i])
         o = int(offsets[i])
         if is_pairs[i]:
-            out = reserve(8 * n)
-            r = rs.rs_request(4, 4, n, 0, 32, k32.data_ptr() + 4 * o, iota.data_ptr(),
-                              ring_base + out, ring_base + out + 4 * n)
-        else:
-            out = reserve(8 * n)
-            r = rs.rs_request(8, 0, n, 0, 64, k64.data_ptr() + 8 * o, None, ring_base + out, None)
-        st, hnd = rs.rs_submit(srv, r)
-        rs.check(st, "rs_submit")
-        reqs.append(r)
-        pending[hnd] = live[-1]
-        if len(reqs) > 4096:
-            reqs = reqs[-4096:]
-    while pending:
-        poll_some(block=True)
-    gc.enable()
-    st, stats = rs.rs_server_stats(srv)
-    rs.check(st, "rs_server_stats")
-    rs.rs_server_destroy(srv)
+            return rs.rs_request(4, 4, n, 0, 32, k32.data_ptr() + 4 * o, iota.data_ptr(),
+                                 ring_base + out, ring_base + out + 4 * n)
+        return rs.rs_request(8, 0, n, 0, 64, k64.data_ptr() + 8 * o, None, ring_base + out, None)
+
+    def serve(idx, paced: bool):
+        """Submit requests idx through a new server (paced: at their arrival
+        times); returns the server's stats and the client's wall time."""
+        st, srv = rs.rs_server_create(budget, streams)
+        rs.check(st, "rs_server_create")
+        pending = {}        # handle -> (ring start, ring end)
+        live = []           # ring regions in use, in allocation order
+        head = 0
+        reqs = []           # keep the ctypes structs alive
+
+        def poll_some(block=False):
+            # one call takes every finished handle off the server's completion
+            # queue; polling each pending handle instead kept the server's lock
+            # busy and starved its scheduler thread
+            st_, finished = rs.rs_server_completed(srv, 4096)
+            rs.check(st_, "rs_server_completed")
+            for hnd in finished:
+                st_, done = rs.rs_poll(srv, hnd)
+                if st_ != rs.RS_OK or not done:
+                    raise SystemExit(f"bench: server request failed: {rs.status_string(st_)}")
+                live.remove(pending.pop(hnd))
+            if block and pending:
+                time.sleep(0.0002)
+
+        def reserve(nbytes):
+            nonlocal head
+            while True:
+                start = head if head + nbytes <= ring_bytes else 0
+                end = start + nbytes
+                if not any(a_ < end and start < b_ for a_, b_ in live):
+                    head = end
+                    live.append((start, end))
+                    return start
+                poll_some(block=True)
+
+        # no cyclic garbage collection while the client keeps the arrival
+        # schedule: a full collection over a large heap stalls it for tens of ms
+        gc.collect()
+        gc.disable()
+        t0 = time.perf_counter()
+        for i in idx:
+            while paced:
+                rem = arrival[i] - (time.perf_counter() - t0)
+                if rem <= 0:
+                    break
+                poll_some()
+                if rem > 3e-4:
+                    time.sleep(1e-4)  # far from the next arrival: leave the lock alone
+            r = request(i, reserve(8 * int(sizes[i])))
+            while True:
+                st, hnd = rs.rs_submit(srv, r)
+                if st != rs.RS_ERR_BUSY:
+                    break
+                poll_some(block=True)  # queue full: wait for completions
+            rs.check(st, "rs_submit")
+            reqs.append(r)
+            pending[hnd] = live[-1]
+            if len(reqs) > 4096:
+                reqs = reqs[-4096:]
+        while pending:
+            poll_some(block=True)
+        wall = time.perf_counter() - t0
+        gc.enable()
+        st, stats = rs.rs_server_stats(srv)
+        rs.check(st, "rs_server_stats")
+        rs.rs_server_destroy(srv)
+        return stats, wall
+
+    stats, _ = serve(range(count), paced=True)
     offered = float(sizes.sum()) / float(arrival[-1]) / 1e9
     link_after = host_link_gbs(torch, ring)
+
+    # capacity: the first compare_requests requests, no arrival schedule
+    sub = list(range(min(compare_requests, count)))
+    sub_keys = float(sizes[sub].sum())
+    sat, sat_wall = serve(sub, paced=False)
+    # plain: one rs_sort_host per request, one stream, same pinned buffers
+    maxn = int(sizes[sub].max())
+    dev_k = torch.empty(maxn * 8, dtype=torch.uint8, device="cuda")
+    dev_v = torch.empty(maxn * 8, dtype=torch.uint8, device="cuda")
+    dev_ka = torch.empty_like(dev_k)
+    dev_va = torch.empty_like(dev_v)
+    need = max(rs.rs_workspace_bytes(4, 4, maxn, 0, 32)[1], rs.rs_workspace_bytes(8, 0, maxn, 0, 64)[1])
+    ws = torch.empty(max(need, 256), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.Stream()
+    h = stream.cuda_stream
+    out = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in sub:
+        n = int(sizes[i])
+        if out + 8 * n > ring_bytes:
+            out = 0
+        r = request(i, out)
+        out += 8 * n
+        st, _ = rs.rs_sort_host(r.key_bytes, r.val_bytes, r.h_keys, r.h_vals, r.h_out_keys,
+                                r.h_out_vals, n, r.begin_bit, r.end_bit, dev_k.data_ptr(),
+                                dev_v.data_ptr() if r.val_bytes else None, dev_ka.data_ptr(),
+                                dev_va.data_ptr() if r.val_bytes else None, ws.data_ptr(),
+                                ws.numel(), h)
+        rs.check(st, "rs_sort_host (plain)")
+    e1.record(stream)
+    stream.synchronize()
+    plain_wall = time.perf_counter() - t0
+    plain_gpu_s = e0.elapsed_time(e1) / 1e3
+    rs.check(rs.rs_workspace_status(ws.data_ptr(), h)[0], "plain device status")
+    del dev_k, dev_v, dev_ka, dev_va, ws
     return {"requests": count, "rate_per_s": rate, "budget_gib": budget / 2**30,
             "streams": streams, "p50_ms": stats["p50_ms"], "p99_ms": stats["p99_ms"],
             "max_ms": stats["max_ms"], "wait_p99_ms": stats["wait_p99_ms"],
@@ -816,6 +927,18 @@ def bench_serving(torch, rs, seconds: float = 10.0, rate: float = 5000.0,
             "offered_gkeys_per_s": offered, "batches": stats["batches"],
             "batched_requests": stats["batched_requests"], "max_queued": stats["max_queued"],
             "pool_peak_gib": stats["pool_peak_bytes"] / 2**30,
+            "served_vs_plain": {
+                "requests": len(sub), "keys": sub_keys,
+                "served_gkeys_per_s": sub_keys / sat_wall / 1e9,
+                "served_p50_ms": sat["p50_ms"], "served_p99_ms": sat["p99_ms"],
+                "served_batches": sat["batches"], "served_batched_requests": sat["batched_requests"],
+                "plain_gkeys_per_s": sub_keys / plain_wall / 1e9,
+                "plain_gpu_gkeys_per_s": sub_keys / plain_gpu_s / 1e9,
+                "served_over_plain": plain_wall / sat_wall,
+                "what": "the first requests of the same trace submitted at once: served = "
+                        "through the server (its capacity); plain = one rs_sort_host call per "
+                        "request on one stream; both from and to pinned host memory, "
+                        "wall-clock first submit -> last completion"},
             "host_link_gb_per_s": {"before": link_before, "after": link_after,
                                    "what": "256 MiB pinned copies, each direction alone"},
             "latency": "submit -> completion callback, host pinned buffers in and out; wait = "

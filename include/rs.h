@@ -178,8 +178,10 @@ rs_status rs_sort_pairs_u64(uint64_t* keys, uint64_t* vals, uint64_t* keys_alt,
                             uint64_t* vals_alt, size_t n, int begin_bit, int end_bit, void* ws,
                             size_t ws_bytes, rs_stream_t stream, int* result_in_alt);
 
-/* Largest n that rs_sort_keys_u32_noalloc accepts. */
+/* Largest n that rs_sort_keys_u32_noalloc accepts, and the size of the
+ * fixed device array that serves as its workspace. */
 #define RS_NOALLOC_MAX_N ((size_t)1 << 23)
+#define RS_NOALLOC_SCRATCH_BYTES ((size_t)9 << 20)
 
 /*
  * rs_sort_keys_u32 without a workspace argument and without allocating.
@@ -188,9 +190,11 @@ rs_status rs_sort_pairs_u64(uint64_t* keys, uint64_t* vals, uint64_t* keys_alt,
  * running inside a framework that owns every device byte through its own
  * pool, real-time or callback contexts where an allocation could block or
  * synchronize the device, and systems whose memory must all be reserved at
- * start-up.  The scratch it needs (9 MiB) is a fixed array of device
- * memory inside this library, present on every GPU that loads the library
- * until the process exits.
+ * start-up.  The scratch it needs (RS_NOALLOC_SCRATCH_BYTES, 9 MiB) is a
+ * fixed array of device memory inside this library, present on every GPU
+ * that loads the library until the process exits.  The tile shape is the
+ * library's usual choice when its workspace fits the array, else the compiled
+ * shape with the smallest workspace; the sorted result is the same.
  *   keys, keys_alt, n, begin_bit, end_bit, stream, result_in_alt: as for
  *   rs_sort_keys_u32; n must not exceed RS_NOALLOC_MAX_N (else RS_ERR_INVALID,
  *   nothing enqueued).
@@ -199,11 +203,22 @@ rs_status rs_sort_pairs_u64(uint64_t* keys, uint64_t* vals, uint64_t* keys_alt,
  * All calls on a device share the one array and each call leaves its
  * contents behind (the next call clears what must start at zero): calls whose
  * work may overlap on the GPU, for example on two streams, race and must be
- * serialized by the caller.  Device-side status words are not reported back
- * by this entry point.
+ * serialized by the caller.  The device address of the array is cached per
+ * device for the life of the CUDA context it was looked up in: do not call
+ * this entry point on a device after cudaDeviceReset of that device.
  */
 rs_status rs_sort_keys_u32_noalloc(uint32_t* keys, uint32_t* keys_alt, size_t n, int begin_bit,
                                    int end_bit, rs_stream_t stream, int* result_in_alt);
+
+/*
+ * Device-side status of the last rs_sort_keys_u32_noalloc call on the current
+ * device: synchronizes `stream` (the stream that call used), then reads the
+ * status word in the library's array.  RS_OK, RS_ERR_TIMEOUT (a bounded wait
+ * ran out) or RS_ERR_DEVICE (an index check failed; the output is not valid);
+ * *info (may be NULL) receives the tile or pass that reported it.  Allocates
+ * nothing.
+ */
+rs_status rs_sort_keys_u32_noalloc_status(rs_stream_t stream, uint32_t* info);
 
 /*
  * Generic form of the four sorts above with an explicit configuration
@@ -216,6 +231,68 @@ rs_status rs_sort_keys_u32_noalloc(uint32_t* keys, uint32_t* keys_alt, size_t n,
 rs_status rs_sort(int key_bytes, int val_bytes, void* keys, void* vals, void* keys_alt,
                   void* vals_alt, size_t n, int begin_bit, int end_bit, const rs_config* cfg,
                   void* ws, size_t ws_bytes, rs_stream_t stream, int* result_in_alt);
+
+/*
+ * End-to-end form of rs_sort for data in host memory: copies the caller's
+ * host arrays into the device buffers, sorts them (Sec. 2.6, as rs_sort) and
+ * copies the sorted arrays back, all enqueued on `stream` in that order.
+ *   h_keys, h_vals          [n] host input (h_vals NULL when val_bytes is 0);
+ *                           read by the copy engine after the call returns
+ *   h_out_keys, h_out_vals  [n] host output; written when the stream's work
+ *                           is done (may alias the input arrays)
+ *   keys, vals, keys_alt, vals_alt, ws: device buffers as for rs_sort (the
+ *                           caller owns them; the result is also left in the
+ *                           pair that *result_in_alt names)
+ * Asynchronous: the host arrays must stay valid until the stream has passed
+ * this call's work (cudaStreamSynchronize, an event).  With page-locked host
+ * memory (cudaHostAlloc / cudaHostRegister) the copies run on the copy
+ * engines and overlap kernels of other streams, so calls on several streams,
+ * each with its own buffers, form a copy-in / sort / copy-out pipeline;
+ * pageable memory makes the copies synchronous.  Argument errors are found
+ * before anything is enqueued (RS_ERR_INVALID, RS_ERR_WORKSPACE);
+ * device-side status as for rs_sort (rs_workspace_status).
+ */
+rs_status rs_sort_host(int key_bytes, int val_bytes, const void* h_keys, const void* h_vals,
+                       void* h_out_keys, void* h_out_vals, size_t n, int begin_bit, int end_bit,
+                       const rs_config* cfg, void* keys, void* vals, void* keys_alt,
+                       void* vals_alt, void* ws, size_t ws_bytes, rs_stream_t stream,
+                       int* result_in_alt);
+
+/*
+ * What the last sort that used workspace `ws` did, read back after `stream`
+ * is done: the digit passes that moved the data and those skipped because
+ * one digit value held every key (Sec. 2.6's counting sort of that digit is
+ * then the identity), the device time of each kernel phase, and the
+ * algorithmic bytes.  Recorded by rs_sort, the four typed sorts,
+ * rs_sort_host and rs_sort_keys_u32_noalloc (whose array has no public
+ * address: its record is not readable).  A segmented sort's workspace gives
+ * form 0; a workspace last used by the sample-sort, merge-sort or server
+ * entry points holds no record.  Times come from the GPU's global timer and
+ * include no host overhead.
+ */
+typedef struct rs_sort_stats {
+  int status;            /* device-side status, as rs_workspace_status returns it */
+  uint32_t info;         /* tile or pass that reported a device-side error */
+  int form;              /* 0: no record; 1: digit histograms + one launch per pass;
+                            2: the whole sort in one cooperative launch; 3: one CTA
+                            (or cluster) holding the array in shared memory */
+  int key_bytes, val_bytes, passes; /* passes = ceil((end_bit - begin_bit) / radix_bits) */
+  uint64_t n;
+  uint32_t moved_mask;   /* bit p: pass p read and wrote the data */
+  uint32_t skipped_mask; /* bit p: pass p was skipped (forms 1 and 2) */
+  double upsweep_ms;     /* forms 1, 2: start until every digit histogram and scan is
+                            done; form 3: the whole sort */
+  double pass_ms[16];    /* forms 1, 2: per moving pass, its first tile taken until its
+                            last CTA finished; 0 for skipped passes */
+  double total_ms;       /* first kernel's start until the last recorded time */
+  double bytes;          /* algorithmic bytes: n K for the histograms plus
+                            2 n (K + V) per moving pass (form 3: 2 n (K + V)) */
+} rs_sort_stats;
+
+/* Synchronizes `stream`, then fills *out.  RS_ERR_INVALID for out NULL;
+ * RS_ERR_CUDA if the synchronization or the read failed.  A workspace that
+ * holds no record (a segmented sort's, one never used) gives form 0. */
+rs_status rs_workspace_stats(const void* ws, rs_stream_t stream, rs_sort_stats* out);
 
 /*
  * Sample sort (Sec. 2.7), the regular-sampling variant after Dehne et al.,
@@ -501,11 +578,30 @@ typedef enum rs_debug_knob {
   RS_DEBUG_TRACE_PTR = 3,         /* device u64 buffer [tiles][16] for onesweep phase data; 0 off */
   RS_DEBUG_TRACE_TILES = 4,       /* number of tiles the trace buffer holds */
   RS_DEBUG_TRACE_PASS = 5,        /* the digit pass whose tiles are traced */
-  RS_DEBUG_LB_SMALL = 6           /* look-back windows of 8 status words instead of 32 */
+  RS_DEBUG_LB_SMALL = 6,          /* look-back windows of 8 status words instead of 32 */
+  RS_DEBUG_BAD_INDEX_TILE = 7     /* debug build only (else RS_ERR_INVALID): this tile of
+                                     digit pass 0 of a multi-launch sort computes scatter
+                                     indices past the array, so that the bounds checks of
+                                     rs_debug_status must catch and drop them; -1 off */
 } rs_debug_knob;
 
 /* Set a knob for later calls from any thread; returns RS_ERR_INVALID for an unknown knob. */
 rs_status rs_debug_set(rs_debug_knob knob, long long value);
+
+/*
+ * Bounds checks of a debug build.  The library built with RS_DEBUG defined
+ * (the package's build step writes it as _build/librs_debug.so beside
+ * librs.so) checks the index of every global store of its kernels against
+ * the length of the array it writes; an index out of range is recorded (the
+ * first one per compiled unit: a store-site number and the index) and the
+ * store is dropped; nothing traps.  This call synchronizes the current
+ * device, then reads and clears those records: RS_ERR_DEVICE if a check
+ * failed since the last call (*site, *index: the first one found), else
+ * RS_OK.  *debug_build (may be NULL) is 1 in a debug build; in a release
+ * build nothing is checked and the call returns RS_OK without touching the
+ * device.  Not part of any sort's status: use it in tests.
+ */
+rs_status rs_debug_status(int* debug_build, uint32_t* site, uint64_t* index);
 
 #ifdef __cplusplus
 }

@@ -3,6 +3,10 @@
 Each translation unit is compiled by its own nvcc process (in parallel),
 then linked into one shared library that exports the C ABI of
 include/rs.h.  A stamp of the sources and flags skips rebuilds.
+
+The debug flavour (_build/librs_debug.so, compiled with RS_DEBUG) checks the
+index of every global store of its kernels (rs_debug_status); the binding
+loads it instead of librs.so when the environment sets RS_LIBRARY=debug.
 """
 from __future__ import annotations
 
@@ -17,6 +21,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(OUT_DIR, "librs.so")
+DEBUG_LIB_PATH = os.path.join(OUT_DIR, "librs_debug.so")
+DEBUG_FLAGS = ("-DRS_DEBUG",)
 INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -48,8 +54,8 @@ def _stamp(extra=()) -> str:
     return h.hexdigest()
 
 
-def _compile(src: str, extra) -> str:
-    obj = os.path.join(OUT_DIR, os.path.basename(src) + ".o")
+def _compile(src: str, extra, suffix: str = ".o") -> str:
+    obj = os.path.join(OUT_DIR, os.path.basename(src) + suffix)
     cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *extra, "-I", INCLUDE, "-c", src, "-o", obj]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
@@ -59,29 +65,45 @@ def _compile(src: str, extra) -> str:
     return obj
 
 
-def build(force: bool = False, extra_flags=(), jobs: int | None = None) -> str:
-    """Compile every translation unit for sm_103a and link librs.so."""
+def _flavours(debug: bool | None):
+    rel = (LIB_PATH, "librs.stamp", ".o", ())
+    dbg = (DEBUG_LIB_PATH, "librs_debug.stamp", ".dbg.o", DEBUG_FLAGS)
+    return {None: [rel, dbg], False: [rel], True: [dbg]}[debug]
+
+
+def build(force: bool = False, extra_flags=(), jobs: int | None = None,
+          debug: bool | None = False) -> str:
+    """Compile every translation unit for sm_103a and link librs.so
+    (debug=True: librs_debug.so; debug=None: both, compiled together).
+    Returns the path of the (first) library."""
     os.makedirs(OUT_DIR, exist_ok=True)
-    stamp_path = os.path.join(OUT_DIR, "librs.stamp")
-    stamp = _stamp(extra_flags)
-    if not force and os.path.exists(LIB_PATH) and os.path.exists(stamp_path):
-        with open(stamp_path) as f:
-            if f.read() == stamp:
-                return LIB_PATH
-    srcs = sources()
-    jobs = jobs or min(len(srcs), max(1, os.cpu_count() or 1))
-    with cf.ThreadPoolExecutor(jobs) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra_flags), srcs))
-    tmp = LIB_PATH + f".tmp{os.getpid()}"
-    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs]
-    res = subprocess.run(cmd, capture_output=True, text=True)
-    if res.returncode != 0:
-        raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")
-    os.replace(tmp, LIB_PATH)
-    with open(stamp_path, "w") as f:
-        f.write(stamp)
-    return LIB_PATH
+    todo = []
+    for lib, stamp_name, suffix, flags in _flavours(debug):
+        stamp_path = os.path.join(OUT_DIR, stamp_name)
+        stamp = _stamp(tuple(extra_flags) + flags)
+        if not force and os.path.exists(lib) and os.path.exists(stamp_path):
+            with open(stamp_path) as f:
+                if f.read() == stamp:
+                    continue
+        todo.append((lib, stamp_path, stamp, suffix, tuple(extra_flags) + flags))
+    if todo:
+        srcs = sources()
+        units = [(src, t) for t in todo for src in srcs]
+        jobs = jobs or min(len(units), max(1, os.cpu_count() or 1))
+        with cf.ThreadPoolExecutor(jobs) as ex:
+            objs = list(ex.map(lambda u: _compile(u[0], u[1][4], u[1][3]), units))
+        for i, (lib, stamp_path, stamp, _, _) in enumerate(todo):
+            tmp = lib + f".tmp{os.getpid()}"
+            mine = objs[i * len(srcs):(i + 1) * len(srcs)]
+            cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *mine]
+            res = subprocess.run(cmd, capture_output=True, text=True)
+            if res.returncode != 0:
+                raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")
+            os.replace(tmp, lib)
+            with open(stamp_path, "w") as f:
+                f.write(stamp)
+    return _flavours(debug)[0][0]
 
 
 if __name__ == "__main__":
-    print(build(force=True))
+    print(build(force=True, debug=None))

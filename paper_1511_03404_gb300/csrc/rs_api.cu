@@ -10,6 +10,8 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/rs.h"
 #include "rs_host.h"
 
@@ -71,6 +73,24 @@ int prepare_kernel(const void* func, int threads, int smem_bytes) {
   return blocks;
 }
 
+// ------------------------------------------------- debug bounds checks
+
+namespace {
+std::mutex& dbg_mu() {
+  static std::mutex m;
+  return m;
+}
+std::vector<DbgReader>& dbg_readers() {
+  static std::vector<DbgReader> v;
+  return v;
+}
+}  // namespace
+
+void register_dbg_reader(DbgReader reader) {
+  std::lock_guard<std::mutex> g(dbg_mu());
+  dbg_readers().push_back(reader);
+}
+
 // ----------------------------------------------------------------- knobs
 
 static std::atomic<long long> g_timeout_ns{1000000000LL};
@@ -80,11 +100,30 @@ static std::atomic<long long> g_trace_ptr{0};
 static std::atomic<long long> g_trace_tiles{0};
 static std::atomic<long long> g_trace_pass{0};
 static std::atomic<long long> g_lb_small{0};
+static std::atomic<long long> g_dbg_bad_tile{-1};
 
 bool pdl_enabled() {
   static const bool on = std::getenv("RS_NO_PDL") == nullptr;
   return on;
 }
+
+bool nvtx_enabled() {
+  static const bool on = std::getenv("RS_NVTX") != nullptr;
+  return on;
+}
+
+void nvtx_push(const char* name) {
+  if (nvtx_enabled()) nvtxRangePushA(name);
+}
+
+void nvtx_pop() {
+  if (nvtx_enabled()) nvtxRangePop();
+}
+
+const char* const kPassNames[kMaxPasses] = {
+    "rs pass 0",  "rs pass 1",  "rs pass 2",  "rs pass 3",  "rs pass 4",  "rs pass 5",
+    "rs pass 6",  "rs pass 7",  "rs pass 8",  "rs pass 9",  "rs pass 10", "rs pass 11",
+    "rs pass 12", "rs pass 13", "rs pass 14", "rs pass 15"};
 
 Knobs knobs_now() {
   Knobs k;
@@ -95,6 +134,7 @@ Knobs knobs_now() {
   k.trace_tiles = uint32_t(g_trace_tiles.load());
   k.trace_pass = int32_t(g_trace_pass.load());
   k.lb_small = int32_t(g_lb_small.load());
+  k.dbg_bad_tile = int32_t(g_dbg_bad_tile.load());
   return k;
 }
 
@@ -275,8 +315,9 @@ rs_status rs_sort(int key_bytes, int val_bytes, void* keys, void* vals, void* ke
     return RS_ERR_INVALID;
   *result_in_alt = 0;
   if (n <= 1 || begin_bit == end_bit) {  // already sorted, nothing moves
+    // clear the status word and the per-call record (no record: form 0)
     if (ws && ws_bytes >= sizeof(Ctrl) &&
-        cudaMemsetAsync(ws, 0, 2 * sizeof(uint32_t), reinterpret_cast<cudaStream_t>(stream)) !=
+        cudaMemsetAsync(ws, 0, sizeof(Ctrl), reinterpret_cast<cudaStream_t>(stream)) !=
             cudaSuccess)
       return RS_ERR_CUDA;
     return RS_OK;
@@ -298,8 +339,67 @@ rs_status rs_sort(int key_bytes, int val_bytes, void* keys, void* vals, void* ke
   a.key_kind = key_kind;
   a.descending = descending;
   int in_alt = 0;
+  nvtx_push("rs_sort");
   const cudaError_t e = v->run(a, &in_alt);
+  nvtx_pop();
   if (e != cudaSuccess) return RS_ERR_CUDA;
+  *result_in_alt = in_alt;
+  return RS_OK;
+}
+
+rs_status rs_sort_host(int key_bytes, int val_bytes, const void* h_keys, const void* h_vals,
+                       void* h_out_keys, void* h_out_vals, size_t n, int begin_bit, int end_bit,
+                       const rs_config* cfg, void* keys, void* vals, void* keys_alt,
+                       void* vals_alt, void* ws, size_t ws_bytes, rs_stream_t stream,
+                       int* result_in_alt) {
+  if (!result_in_alt || !valid_types(key_bytes, val_bytes)) return RS_ERR_INVALID;
+  *result_in_alt = 0;
+  if (n > RS_MAX_N) return RS_ERR_INVALID;
+  if (n > 0 && (!h_keys || !h_out_keys || !keys)) return RS_ERR_INVALID;
+  if (n > 0 && (val_bytes != 0) != (h_vals != nullptr && h_out_vals != nullptr && vals != nullptr))
+    return RS_ERR_INVALID;
+  if (val_bytes == 0 && (h_vals || h_out_vals)) return RS_ERR_INVALID;
+  // every argument the sort checks is checked before anything is enqueued
+  size_t need = 0;
+  rs_status st = rs_workspace_bytes(key_bytes, val_bytes, n, begin_bit, end_bit, cfg, &need);
+  if (st != RS_OK) return st;
+  if (n <= 1 || begin_bit == end_bit) {  // nothing moves: the input is the output
+    if (n == 0) return rs_sort(key_bytes, val_bytes, keys, vals, keys_alt, vals_alt, n,
+                               begin_bit, end_bit, cfg, ws, ws_bytes, stream, result_in_alt);
+  } else {
+    if ((val_bytes == 0) != (vals_alt == nullptr) || !keys_alt || keys == keys_alt)
+      return RS_ERR_INVALID;
+    if (!aligned(keys, key_bytes) || !aligned(keys_alt, key_bytes)) return RS_ERR_INVALID;
+    if (val_bytes && (vals == vals_alt || !aligned(vals, val_bytes) || !aligned(vals_alt, val_bytes)))
+      return RS_ERR_INVALID;
+    if (cfg && (cfg->key_kind < RS_KEY_UNSIGNED || cfg->key_kind > RS_KEY_FLOAT ||
+                (cfg->descending & ~1)))
+      return RS_ERR_INVALID;
+    if (need > 0 && (!ws || ws_bytes < need || !aligned(ws, 256))) return RS_ERR_WORKSPACE;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const size_t kbytes = n * size_t(key_bytes), vbytes = n * size_t(val_bytes);
+  nvtx_push("rs_sort_host");
+  if (cudaMemcpyAsync(keys, h_keys, kbytes, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      (vbytes && cudaMemcpyAsync(vals, h_vals, vbytes, cudaMemcpyHostToDevice, s) != cudaSuccess)) {
+    nvtx_pop();
+    return RS_ERR_CUDA;
+  }
+  int in_alt = 0;
+  st = rs_sort(key_bytes, val_bytes, keys, vals, keys_alt, vals_alt, n, begin_bit, end_bit, cfg,
+               ws, ws_bytes, stream, &in_alt);
+  if (st != RS_OK) {
+    nvtx_pop();
+    return st;
+  }
+  const void* rk = in_alt ? keys_alt : keys;
+  const void* rv = in_alt ? vals_alt : vals;
+  if (cudaMemcpyAsync(h_out_keys, rk, kbytes, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      (vbytes && cudaMemcpyAsync(h_out_vals, rv, vbytes, cudaMemcpyDeviceToHost, s) != cudaSuccess)) {
+    nvtx_pop();
+    return RS_ERR_CUDA;
+  }
+  nvtx_pop();
   *result_in_alt = in_alt;
   return RS_OK;
 }
@@ -378,6 +478,72 @@ rs_status rs_workspace_status(const void* ws, rs_stream_t stream, uint32_t* info
     case 1u: return RS_ERR_INVALID;  // e.g. segment offsets that do not describe the array
     default: return RS_ERR_DEVICE;
   }
+}
+
+rs_status rs_workspace_stats(const void* ws, rs_stream_t stream, rs_sort_stats* out) {
+  if (!out) return RS_ERR_INVALID;
+  std::memset(out, 0, sizeof(*out));
+  out->status = rs_workspace_status(ws, stream, &out->info);
+  if (out->status == RS_ERR_CUDA || !ws) return out->status == RS_ERR_CUDA ? RS_ERR_CUDA : RS_OK;
+  Ctrl c;
+  if (cudaMemcpy(&c, ws, sizeof(c), cudaMemcpyDeviceToHost) != cudaSuccess) return RS_ERR_CUDA;
+  const int form = int(c.stat_shape >> 24);
+  if (form < 1 || form > 3) return RS_OK;  // this call left no record (see the header)
+  out->form = form;
+  out->key_bytes = int(c.stat_shape & 0xffu);
+  out->val_bytes = int((c.stat_shape >> 8) & 0xffu);
+  out->passes = int((c.stat_shape >> 16) & 0xffu);
+  out->n = c.stat_n;
+  if (out->passes < 1 || out->passes > kMaxPasses) {
+    out->form = 0;
+    return RS_OK;
+  }
+  const uint32_t all = out->passes >= 32 ? ~0u : ((1u << out->passes) - 1u);
+  out->moved_mask = c.exec_mask & all;
+  out->skipped_mask = all & ~out->moved_mask;
+  const double kb = out->key_bytes, vb = out->val_bytes, n = double(out->n);
+  out->upsweep_ms = c.t_upsweep * 1e-6;
+  uint32_t last = c.t_upsweep;
+  for (int p = 0; p < out->passes; ++p) {
+    if (c.t_pass[p][1] > c.t_pass[p][0] && c.t_pass[p][0] > 0)
+      out->pass_ms[p] = (c.t_pass[p][1] - c.t_pass[p][0]) * 1e-6;
+    last = std::max(last, c.t_pass[p][1]);
+  }
+  out->total_ms = last * 1e-6;
+  if (form == 3)
+    out->bytes = 2.0 * n * (kb + vb);  // one read and one write; the passes stay on chip
+  else
+    out->bytes = n * kb + double(__builtin_popcount(out->moved_mask)) * 2.0 * n * (kb + vb);
+  return RS_OK;
+}
+
+rs_status rs_debug_status(int* debug_build, uint32_t* site, uint64_t* index) {
+#ifdef RS_DEBUG
+  const int is_debug = 1;
+#else
+  const int is_debug = 0;
+#endif
+  if (debug_build) *debug_build = is_debug;
+  if (site) *site = 0;
+  if (index) *index = 0;
+  if (!is_debug) return RS_OK;
+  if (cudaDeviceSynchronize() != cudaSuccess) return RS_ERR_CUDA;
+  std::vector<DbgReader> readers;
+  {
+    std::lock_guard<std::mutex> g(dbg_mu());
+    readers = dbg_readers();
+  }
+  rs_status st = RS_OK;
+  for (DbgReader r : readers) {
+    uint64_t w = 0;
+    if (!r(&w)) return RS_ERR_CUDA;
+    if ((w >> 63) && st == RS_OK) {
+      st = RS_ERR_DEVICE;
+      if (site) *site = uint32_t((w >> 48) & 0x7fffu);
+      if (index) *index = w & ((uint64_t(1) << 48) - 1);
+    }
+  }
+  return st;
 }
 
 rs_status rs_profile_begin(int capacity) {
@@ -485,6 +651,13 @@ rs_status rs_debug_set(rs_debug_knob knob, long long value) {
     case RS_DEBUG_LB_SMALL:
       g_lb_small.store(value);
       return RS_OK;
+    case RS_DEBUG_BAD_INDEX_TILE:
+#ifdef RS_DEBUG
+      g_dbg_bad_tile.store(value < 0 ? -1 : value);
+      return RS_OK;
+#else
+      return RS_ERR_INVALID;  // only a build that checks every store index takes it
+#endif
   }
   return RS_ERR_INVALID;
 }

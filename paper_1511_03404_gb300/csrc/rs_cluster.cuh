@@ -90,9 +90,14 @@ __global__ void __launch_bounds__(THREADS, 1)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t rank = cluster_ctarank();
   const uint32_t ncta = gridDim.x;  // the grid is one cluster
+  const int passes = (end_bit - begin_bit + RADIX_BITS - 1) / RADIX_BITS;
   if (ctrl != nullptr && blockIdx.x == 0 && tid == 0) {
     ctrl->error = 0u;
     ctrl->error_info = 0u;
+    ctrl->exec_mask = (1u << passes) - 1u;  // every pass runs (in shared memory)
+    stat_clear_times(ctrl);
+    stat_begin(ctrl, n, uint32_t(sizeof(K)) | uint32_t(VB) << 8 | uint32_t(passes) << 16 |
+                            3u << 24);
   }
 
   // load this CTA's slice (transformed keys; the largest key past the end)
@@ -173,10 +178,14 @@ __global__ void __launch_bounds__(THREADS, 1)
   const V* vs = s_v + src * SLICE;
   for (uint32_t i = tid; i < uint32_t(SLICE); i += THREADS) {
     const uint32_t g = base0 + i;
-    if (g < n) {
+    if (g < n && dbg_ok(g, n, kSiteClusterOut)) {
       keys[g] = xf.on ? xf_inv(ks[i], xf) : ks[i];
       if constexpr (VB > 0) vals[g] = vs[i];
     }
+  }
+  if (ctrl != nullptr) {
+    __syncthreads();
+    if (tid == 0) atomicMax(&ctrl->t_upsweep, stat_now(ctrl));
   }
 }
 

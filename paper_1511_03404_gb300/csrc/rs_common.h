@@ -38,7 +38,15 @@ struct Ctrl {
   uint32_t exec_mask;   // bit p: pass p moves the data (written by the upsweep's last CTA)
   uint32_t tile_counter[kMaxPasses];  // dynamic tile ids of each pass
   uint32_t grid_bar;    // arrivals at the grid barriers of a one-launch sort
-  uint32_t reserved[64 - 5 - kMaxPasses];
+  // Record of the call for rs_workspace_stats (zeroed with the rest of the
+  // block at the start of every multi-launch sort).  Times are %globaltimer
+  // nanoseconds after t0, the upsweep's start.
+  uint32_t stat_n;       // elements sorted
+  uint32_t stat_shape;   // key bytes | value bytes << 8 | passes << 16 | 1 << 24 (recorded)
+  uint32_t t0_lo, t0_hi; // %globaltimer when the upsweep started
+  uint32_t t_upsweep;    // upsweep's last CTA done
+  uint32_t t_pass[kMaxPasses][2];  // per pass: first tile taken, last CTA done
+  uint32_t reserved[64 - 5 - kMaxPasses - 5 - 2 * kMaxPasses];
 };
 static_assert(sizeof(Ctrl) == 256, "Ctrl must be 256 bytes");
 
@@ -51,6 +59,8 @@ struct Knobs {
   uint32_t trace_tiles;    // tiles 0 .. trace_tiles-1 of trace_pass are recorded
   int32_t trace_pass;
   int32_t lb_small;        // test-only: look-back windows of 8 instead of 32 words
+  int32_t dbg_bad_tile;    // debug builds only: this tile of pass 0 computes scatter
+                           // indices past the array, which the bounds checks drop (-1: off)
 };
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }

@@ -57,7 +57,8 @@ __global__ void __launch_bounds__(THREADS, MINB)
             uint32_t* __restrict__ counts, uint32_t* __restrict__ status,
             uint32_t* __restrict__ gagg, uint32_t* __restrict__ ginc, uint32_t tiles,
             uint32_t tiles_pad, uint32_t groups_pad, uint4* __restrict__ zero_base,
-            uint64_t zero_vec4, Ctrl* __restrict__ ctrl, Knobs knobs, KeyXf<K> xf) {
+            uint64_t zero_vec4, Ctrl* __restrict__ ctrl, Knobs knobs, KeyXf<K> xf,
+            uint32_t shape) {
   using F = FusedSmem<K, VB, RADIX_BITS, THREADS, ITEMS>;
   using S = typename F::S;
   constexpr int RADIX = F::RADIX, MAXP = F::MAXP;
@@ -68,6 +69,8 @@ __global__ void __launch_bounds__(THREADS, MINB)
   uint32_t* s_off = reinterpret_cast<uint32_t*>(smem + F::OFF);
   uint32_t* s_flag = reinterpret_cast<uint32_t*>(smem + F::FLAG);
   const int tid = threadIdx.x;
+  const bool rec = blockIdx.x == 0 && tid == 0;  // keeps the per-call record
+  if (rec) stat_begin(ctrl, n, shape);
 
   // ---- 1. histograms of every pass, and the look-back words cleared
   for (int i = tid; i < passes * RADIX; i += THREADS) s_hist[i] = 0u;
@@ -92,10 +95,11 @@ __global__ void __launch_bounds__(THREADS, MINB)
     count_all(std::false_type{});
   for (uint64_t i = uint64_t(blockIdx.x) * THREADS + tid; i < zero_vec4;
        i += uint64_t(gridDim.x) * THREADS)
-    zero_base[i] = make_uint4(0u, 0u, 0u, 0u);
+    if (dbg_ok(i, zero_vec4, kSiteFusedClear)) zero_base[i] = make_uint4(0u, 0u, 0u, 0u);
   __syncthreads();
   for (int w = tid; w < passes * RADIX; w += THREADS)
-    if (s_hist[w]) atomicAdd(&counts[w], s_hist[w]);
+    if (s_hist[w] && dbg_ok(w, uint64_t(passes) * RADIX, kSiteFusedCounts))
+      atomicAdd(&counts[w], s_hist[w]);
   uint32_t gen = 1;
   if (!grid_barrier(ctrl, gen, knobs.timeout_ns, s_flag)) return;
 
@@ -111,7 +115,10 @@ __global__ void __launch_bounds__(THREADS, MINB)
     const uint32_t skipped = ~exec & ((1u << passes) - 1u);
     exec |= skipped & (0u - skipped);
   }
-  if (blockIdx.x == 0 && tid == 0) ctrl->exec_mask = exec;
+  if (rec) {
+    ctrl->exec_mask = exec;
+    ctrl->t_upsweep = stat_now(ctrl);
+  }
 
   // ---- 3. the passes that move data
   for (int p = 0; p < passes; ++p) {
@@ -132,10 +139,13 @@ __global__ void __launch_bounds__(THREADS, MINB)
     t.gagg = gagg + size_t(p) * groups_pad * RADIX;
     t.ginc = ginc + size_t(p) * groups_pad * RADIX;
     t.tiles = tiles;
+    t.lb_words = uint64_t(tiles_pad) * RADIX;
+    t.g_words = uint64_t(groups_pad) * RADIX;
     t.lb_small = knobs.lb_small != 0;
     t.xf = xf;
     t.xin = xf.on && p == __ffs(int(exec)) - 1;
     t.xout = xf.on && p == 31 - __clz(exec);
+    if (rec) ctrl->t_pass[p][0] = stat_now(ctrl);
     for (;;) {
       __syncthreads();  // the previous tile is done with s_misc
       if (tid == 0) {
@@ -147,11 +157,13 @@ __global__ void __launch_bounds__(THREADS, MINB)
       if (tile >= tiles) break;  // CTA-uniform
       t.tile = tile;
       t.silent = (int(tile) == knobs.drop_tile) && (p == knobs.drop_pass);
+      t.dbg_bad = false;
       t.trace = nullptr;
       onesweep_tile<K, VB, RADIX_BITS, THREADS, ITEMS, true>(t, ctrl, knobs.timeout_ns, smem);
     }
     ++gen;
     if (!grid_barrier(ctrl, gen, knobs.timeout_ns, s_flag)) return;
+    if (rec) ctrl->t_pass[p][1] = stat_now(ctrl);
   }
 }
 

@@ -74,6 +74,20 @@ void prof_after(cudaStream_t s, int kind, double bytes, int mask_slot = -1, int 
 // Current fault-injection / wait-limit settings (rs_debug_set).
 Knobs knobs_now();
 
+// NVTX ranges around the library's calls and launches, for timeline tools
+// (nsys, ncu --nvtx): on when the environment sets RS_NVTX (read once).
+bool nvtx_enabled();
+void nvtx_push(const char* name);
+void nvtx_pop();
+// "rs pass 0" ... "rs pass 15"
+extern const char* const kPassNames[kMaxPasses];
+
+// Debug builds: every translation unit with kernels registers a reader of its
+// bounds-check word (rs_debug.cuh); rs_debug_status calls them all.  A
+// reader returns false when the read failed.
+using DbgReader = bool (*)(uint64_t* word);
+void register_dbg_reader(DbgReader reader);
+
 inline int num_passes(int begin_bit, int end_bit, int radix_bits) {
   return (end_bit - begin_bit + radix_bits - 1) / radix_bits;
 }

@@ -24,6 +24,7 @@
 #include <type_traits>
 
 #include "rs_common.h"
+#include "rs_debug.cuh"
 
 namespace rs {
 
@@ -163,6 +164,31 @@ __device__ __forceinline__ void report_error(Ctrl* ctrl, uint32_t code, uint32_t
   if (atomicCAS(&ctrl->error, 0u, code) == 0u) atomicExch(&ctrl->error_info, info);
 }
 
+// Per-call record read by rs_workspace_stats: the shape of the sort and the
+// %globaltimer start of its first kernel (one thread), then times relative
+// to that start, at least 1 so that 0 means "not reached".
+__device__ __forceinline__ void stat_begin(Ctrl* ctrl, uint32_t n, uint32_t shape) {
+  const uint64_t t = global_ns();
+  ctrl->t0_lo = uint32_t(t);
+  ctrl->t0_hi = uint32_t(t >> 32);
+  ctrl->stat_n = n;
+  ctrl->stat_shape = shape;
+}
+
+// The forms that do not start from a cleared control block clear the
+// record's times themselves (one thread, before any other writes them).
+__device__ __forceinline__ void stat_clear_times(Ctrl* ctrl) {
+  ctrl->t_upsweep = 0u;
+#pragma unroll
+  for (int p = 0; p < kMaxPasses; ++p) ctrl->t_pass[p][0] = ctrl->t_pass[p][1] = 0u;
+}
+
+__device__ __forceinline__ uint32_t stat_now(const Ctrl* ctrl) {
+  const uint64_t t0 = (uint64_t(ctrl->t0_hi) << 32) | ctrl->t0_lo;
+  const uint64_t d = global_ns() - t0;
+  return d >= 0xffffffffull ? 0xffffffffu : (d == 0 ? 1u : uint32_t(d));
+}
+
 // Programmatic dependent launch.  A kernel launched with programmatic stream
 // serialization may start while the kernel before it on the stream is still
 // running; pdl_wait() blocks (in hardware) until that kernel has completed and
@@ -268,7 +294,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     k_upsweep(const K* __restrict__ keys, uint32_t n, int begin_bit, int end_bit, int passes,
               uint32_t* __restrict__ counts, uint32_t* __restrict__ offsets,
               Ctrl* __restrict__ ctrl, uint4* __restrict__ zero_base, uint64_t zero_vec4,
-              KeyXf<K> xf, bool early_dependents) {
+              KeyXf<K> xf, bool early_dependents, uint32_t shape) {
   constexpr int RADIX = 1 << RADIX_BITS;
   constexpr int SLOTS = sizeof(K) == 4 ? 32 : 16;
   constexpr int VEC = 16 / int(sizeof(K));
@@ -284,6 +310,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (early_dependents) pdl_launch_dependents();
 
   const int tid = threadIdx.x, lane = tid & 31;
+  if (shape != 0u && blockIdx.x == 0 && tid == 0) stat_begin(ctrl, n, shape);
   const uint32_t slot = uint32_t(lane & (SLOTS - 1));
   uint32_t shiftp[MAXP], maskp[MAXP];
 #pragma unroll
@@ -359,12 +386,12 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint32_t c = 0u;
 #pragma unroll 8
     for (int l = 0; l < SLOTS; ++l) c += row[(l + lane) & (SLOTS - 1)];  // rotated: no bank conflicts
-    if (c) atomicAdd(&counts[w], c);
+    if (c && dbg_ok(w, uint64_t(passes) * RADIX, kSiteUpCounts)) atomicAdd(&counts[w], c);
   }
 
   // clear the look-back status words of every pass of this call
   for (uint64_t i = uint64_t(blockIdx.x) * THREADS + tid; i < zero_vec4; i += stride)
-    zero_base[i] = make_uint4(0u, 0u, 0u, 0u);
+    if (dbg_ok(i, zero_vec4, kSiteUpClear)) zero_base[i] = make_uint4(0u, 0u, 0u, 0u);
 
   // last CTA: scan each histogram, choose the passes that move data
   __threadfence();
@@ -377,7 +404,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   for (int p = 0; p < passes; ++p) {
     const uint32_t c = tid < RADIX ? ld_relaxed(&counts[p * RADIX + tid]) : 0u;
     const uint32_t e = block_exclusive_scan<THREADS>(c, s_tot);
-    if (tid < RADIX) offsets[p * RADIX + tid] = e;
+    if (tid < RADIX && dbg_ok(uint64_t(p) * RADIX + tid, uint64_t(passes) * RADIX, kSiteUpOffsets))
+      offsets[p * RADIX + tid] = e;
     // a pass in which one digit value holds every key leaves the order as it is
     const int one_digit = __syncthreads_or(tid < RADIX && c == n);
     if (!one_digit) exec |= 1u << p;
@@ -390,6 +418,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       exec |= skipped & (0u - skipped);
     }
     ctrl->exec_mask = exec;
+    if (shape != 0u) ctrl->t_upsweep = stat_now(ctrl);
   }
 }
 
@@ -443,8 +472,11 @@ struct TileArgs {
   uint32_t* gagg;               // [groups/4][RADIX][4] group counts of this pass, or null (flat walk)
   uint32_t* ginc;               // [groups/4][RADIX][4] group inclusive prefixes of this pass
   uint32_t tiles;               // tiles of this array
+  uint64_t lb_words;            // words in status (debug bounds checks only)
+  uint64_t g_words;             // words in gagg / ginc (debug bounds checks only)
   bool silent;                  // test-only: publish nothing for this tile
   bool lb_small;                // test-only: 8-word look-back windows
+  bool dbg_bad;                 // debug builds, test-only: scatter indices pushed past n
   uint64_t* trace;              // test-only: 16 phase stamps / counters of this tile, or null
   KeyXf<K> xf;                  // order-preserving key transform of the sort
   bool xin;                     // the source holds untransformed keys: apply xf on load
@@ -780,9 +812,11 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
     for (int w = 0; w < UNITS; ++w) run += s_wh[w * RADIX + tid] >> CSHIFT;
     my_cnt = run;
     if (!t.silent) {
-      st_relaxed(&t.status[lb_index<RADIX>(t.tile0 + tile, tid)],
-                 (tile == 0u ? kFlagInc : kFlagAgg) | run);
-      if (t.gagg != nullptr)
+      if (dbg_ok(lb_index<RADIX>(t.tile0 + tile, tid), t.lb_words, kSiteTileStatus))
+        st_relaxed(&t.status[lb_index<RADIX>(t.tile0 + tile, tid)],
+                   (tile == 0u ? kFlagInc : kFlagAgg) | run);
+      if (t.gagg != nullptr &&
+          dbg_ok(lb_index<RADIX>(tile / kGroupTiles, tid), t.g_words, kSiteGroupAgg))
         atomicAdd(&t.gagg[lb_index<RADIX>(tile / kGroupTiles, tid)], run | kGroupOne);
     }
   }
@@ -897,12 +931,13 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
         // a walk that ran past group 0 without an inclusive prefix has summed
         // every earlier group completely
       }
-      if (!t.silent)
+      if (!t.silent && dbg_ok(lb_index<RADIX>(t.tile0 + tile, tid), t.lb_words, kSiteTileStatus))
         st_relaxed(&t.status[lb_index<RADIX>(t.tile0 + tile, tid)],
                    gave_up ? kFlagErr : (kFlagInc | ((excl + my_cnt) & kValueMask)));
     }
     if (t.ginc != nullptr && !t.silent &&
-        ((tile + 1) % kGroupTiles == 0 || tile + 1 == t.tiles))
+        ((tile + 1) % kGroupTiles == 0 || tile + 1 == t.tiles) &&
+        dbg_ok(lb_index<RADIX>(tile / kGroupTiles, tid), t.g_words, kSiteGroupInc))
       st_relaxed(&t.ginc[lb_index<RADIX>(tile / kGroupTiles, tid)],
                  gave_up ? kFlagErr : (kFlagInc | ((excl + my_cnt) & kValueMask)));
     // every key of digit tid goes to [pass offset + excl, ... + its count):
@@ -955,6 +990,9 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
   const bool full = tile_len == uint32_t(TILE);
   uint32_t gidx[VB > 0 ? ITEMS : 1];  // the values' destinations
   // XO: the last pass that moves data writes the keys back untransformed
+  // debug builds, test-only: every destination of this tile past the array,
+  // so that the bounds checks must drop the stores (0 otherwise)
+  const uint32_t dbg_push = (kDebugChecks && t.dbg_bad) ? n : 0u;
   auto scatter_keys = [&](auto XO) {
     auto out = [&](K k) {
       if constexpr (decltype(XO)::value) return xf_inv(k, t.xf);
@@ -965,8 +1003,8 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
       for (int s = 0; s < ITEMS; ++s) {
         const uint32_t i = uint32_t(s * THREADS + tid);
         const K k = s_out[i];
-        const uint32_t g = s_gbase[digit_of(k, t.shift, t.mask)] + i;
-        t.kdst[g] = out(k);
+        const uint32_t g = s_gbase[digit_of(k, t.shift, t.mask)] + i + dbg_push;
+        if (dbg_ok(g, n, kSiteKeyScatter)) t.kdst[g] = out(k);
         if constexpr (VB > 0) gidx[s] = g;
       }
     } else {
@@ -976,8 +1014,8 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
         if constexpr (VB > 0) gidx[s] = 0u;
         if (i < tile_len) {
           const K k = s_out[i];
-          const uint32_t g = s_gbase[digit_of(k, t.shift, t.mask)] + i;
-          t.kdst[g] = out(k);
+          const uint32_t g = s_gbase[digit_of(k, t.shift, t.mask)] + i + dbg_push;
+          if (dbg_ok(g, n, kSiteKeyScatter)) t.kdst[g] = out(k);
           if constexpr (VB > 0) gidx[s] = g;
         }
       }
@@ -1013,12 +1051,13 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
       }
       if (full) {
 #pragma unroll
-        for (int s = 0; s < ITEMS; ++s) t.vdst[gidx[s]] = s_vout[s * THREADS + tid];
+        for (int s = 0; s < ITEMS; ++s)
+          if (dbg_ok(gidx[s], n, kSiteValScatter)) t.vdst[gidx[s]] = s_vout[s * THREADS + tid];
       } else {
 #pragma unroll
         for (int s = 0; s < ITEMS; ++s) {
           const uint32_t i = uint32_t(s * THREADS + tid);
-          if (i < tile_len) t.vdst[gidx[s]] = s_vout[i];
+          if (i < tile_len && dbg_ok(gidx[s], n, kSiteValScatter)) t.vdst[gidx[s]] = s_vout[i];
         }
       }
     } else {
@@ -1060,6 +1099,7 @@ __global__ void __launch_bounds__(THREADS, MINB)
   if (threadIdx.x == 0) {
     s_misc[0] = atomicAdd(&ctrl->tile_counter[pass], 1u);
     s_misc[2] = ld_relaxed(&ctrl->error);  // an earlier pass of this call gave up
+    if (s_misc[0] == 0u) ctrl->t_pass[pass][0] = stat_now(ctrl);
   }
   __syncthreads();
   if (s_misc[2] != 0u) return;  // CTA-uniform
@@ -1078,7 +1118,10 @@ __global__ void __launch_bounds__(THREADS, MINB)
   t.gagg = gagg;
   t.ginc = ginc;
   t.tiles = tiles;
+  t.lb_words = uint64_t((tiles + 3u) / 4u * 4u) * S::RADIX;
+  t.g_words = uint64_t((tiles + kGroupTiles - 1) / kGroupTiles + 3u) / 4u * 4u * S::RADIX;
   t.silent = (int(t.tile) == knobs.drop_tile) && (pass == knobs.drop_pass);
+  t.dbg_bad = kDebugChecks && int(t.tile) == knobs.dbg_bad_tile && pass == 0;
   t.lb_small = knobs.lb_small != 0;
   t.trace = (knobs.trace != nullptr && pass == knobs.trace_pass && t.tile < knobs.trace_tiles)
                 ? knobs.trace + size_t(t.tile) * 16
@@ -1088,6 +1131,8 @@ __global__ void __launch_bounds__(THREADS, MINB)
   t.xout = xf.on && pass == 31 - __clz(exec);
   onesweep_tile<K, VB, RADIX_BITS, THREADS, ITEMS, false, false, UNIT>(t, ctrl, knobs.timeout_ns,
                                                                       smem);
+  __syncthreads();
+  if (threadIdx.x == 0) atomicMax(&ctrl->t_pass[pass][1], stat_now(ctrl));
 }
 
 // One digit pass with resident CTAs (a grid of SMs x resident CTAs): each CTA
@@ -1119,6 +1164,7 @@ __global__ void __launch_bounds__(THREADS, MINB)
     if constexpr (VB > 0) mbar_init(&s_bar[1]);
     s_misc[3] = atomicAdd(pf.counter, 1u);
     s_misc[2] = ld_relaxed(&ctrl->error);  // an earlier pass of this call gave up
+    if (s_misc[3] == 0u) ctrl->t_pass[pass][0] = stat_now(ctrl);
   }
   __syncthreads();
   TileArgs<K, VB> t;
@@ -1135,6 +1181,8 @@ __global__ void __launch_bounds__(THREADS, MINB)
   t.gagg = gagg;
   t.ginc = ginc;
   t.tiles = tiles;
+  t.lb_words = uint64_t((tiles + 3u) / 4u * 4u) * S::RADIX;
+  t.g_words = uint64_t((tiles + kGroupTiles - 1) / kGroupTiles + 3u) / 4u * 4u * S::RADIX;
   t.lb_small = knobs.lb_small != 0;
   t.xf = xf;
   t.xin = xf.on && pass == __ffs(int(exec)) - 1;  // first and last pass that move data
@@ -1150,6 +1198,7 @@ __global__ void __launch_bounds__(THREADS, MINB)
   for (uint32_t it = 0; tile < tiles; ++it) {
     t.tile = tile;
     t.silent = (int(tile) == knobs.drop_tile) && (pass == knobs.drop_pass);
+    t.dbg_bad = kDebugChecks && int(tile) == knobs.dbg_bad_tile && pass == 0;
     t.trace = (knobs.trace != nullptr && pass == knobs.trace_pass && tile < knobs.trace_tiles)
                   ? knobs.trace + size_t(tile) * 16
                   : nullptr;
@@ -1175,6 +1224,7 @@ __global__ void __launch_bounds__(THREADS, MINB)
   if (threadIdx.x == 0) {
     mbar_inval(&s_bar[0]);
     if constexpr (VB > 0) mbar_inval(&s_bar[1]);
+    atomicMax(&ctrl->t_pass[pass][1], stat_now(ctrl));
   }
 }
 
@@ -1266,7 +1316,7 @@ __device__ __forceinline__ void cta_sort(const K* kin, const ValT<VB>* vin, K* k
 #pragma unroll
   for (int j = 0; j < ITEMS; ++j) {
     const uint32_t i = slot0 + j * 32;
-    if (i < len) {
+    if (i < len && dbg_ok(i, len, kSiteSmallOut)) {
       kout[i] = xf.on ? xf_inv(key[j], xf) : key[j];
       if constexpr (VB > 0) vout[i] = val[j];
     }
@@ -1280,12 +1330,19 @@ __global__ void __launch_bounds__(THREADS, 1)
     k_small_sort(K* keys, ValT<VB>* vals, uint32_t n, int begin_bit, int end_bit, Ctrl* ctrl,
                  KeyXf<K> xf) {
   extern __shared__ __align__(16) unsigned char smem[];
+  const int passes = (end_bit - begin_bit + RADIX_BITS - 1) / RADIX_BITS;
   if (ctrl != nullptr && threadIdx.x == 0) {
     ctrl->error = 0u;
     ctrl->error_info = 0u;
+    ctrl->exec_mask = (1u << passes) - 1u;  // every pass runs (in shared memory)
+    stat_clear_times(ctrl);
+    stat_begin(ctrl, n, uint32_t(sizeof(K)) | uint32_t(VB) << 8 | uint32_t(passes) << 16 |
+                            3u << 24);
   }
   cta_sort<K, VB, RADIX_BITS, THREADS, ITEMS>(keys, vals, keys, vals, n, begin_bit, end_bit,
                                               smem, xf);
+  __syncthreads();
+  if (ctrl != nullptr && threadIdx.x == 0) ctrl->t_upsweep = stat_now(ctrl);
 }
 
 }  // namespace rs

@@ -33,8 +33,9 @@ struct OnesweepSort {
 
   // early: the kernel after this one (the first pass) may be scheduled as
   // soon as this one starts, because its grid fills the GPU anyway
+  // shape: the per-call record of rs_workspace_stats (0: none)
   static cudaError_t upsweep(const SortArgs& a, int passes, const Layout& L, bool clear_status,
-                             bool early = false) {
+                             bool early = false, uint32_t shape = 0u) {
     char* ws = static_cast<char*>(a.ws);
     Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws);
     cudaError_t e = cudaMemsetAsync(ws, 0, L.memset_bytes, a.stream);
@@ -57,7 +58,7 @@ struct OnesweepSort {
         static_cast<const K*>(a.keys), a.n, a.begin_bit, a.end_bit, passes,
         reinterpret_cast<uint32_t*>(ws + L.counts), reinterpret_cast<uint32_t*>(ws + L.offsets),
         ctrl, reinterpret_cast<uint4*>(ws + L.status), zero_vec4,
-        make_key_xf<K>(a.key_kind, a.descending), early);
+        make_key_xf<K>(a.key_kind, a.descending), early, shape);
     e = cudaGetLastError();
     prof_after(a.stream, 0, double(a.n) * sizeof(K));
     return e;
@@ -81,7 +82,11 @@ struct OnesweepSort {
     // let in only as the kernel before it exits
     const bool pdl = pdl_enabled();
     const bool fills = pdl && (PERSIST || nt > size_t(device_info().sms) * occ);
-    cudaError_t e = upsweep(a, passes, L, true, fills);
+    const uint32_t shape = uint32_t(sizeof(K)) | uint32_t(VB) << 8 | uint32_t(passes) << 16 |
+                           1u << 24;
+    nvtx_push("rs upsweep");
+    cudaError_t e = upsweep(a, passes, L, true, fills, shape);
+    nvtx_pop();
     if (e != cudaSuccess) return e;
     char* ws = static_cast<char*>(a.ws);
     Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws);
@@ -108,6 +113,7 @@ struct OnesweepSort {
       attr[0].val.programmaticStreamSerializationAllowed = 1;
       cfg.attrs = attr;
       cfg.numAttrs = pdl ? 1 : 0;
+      nvtx_push(kPassNames[p]);
       e = cudaLaunchKernelEx(
           &cfg, kern, static_cast<K*>(a.keys), static_cast<K*>(a.keys_alt),
           static_cast<V*>(a.vals), static_cast<V*>(a.vals_alt), a.n, p, uint32_t(lo), mask,
@@ -118,6 +124,7 @@ struct OnesweepSort {
           reinterpret_cast<uint32_t*>(ws + L.ginc) + size_t(p) * L.groups * RADIX, uint32_t(nt),
           ctrl, a.knobs, xf, fills);
       if (e == cudaSuccess) e = cudaGetLastError();
+      nvtx_pop();
       prof_after(a.stream, 1, bytes, slot, p);
       if (e != cudaSuccess) return e;
     }
@@ -184,8 +191,10 @@ struct FusedSort {
     uint64_t zero_vec4 = L.status_bytes / 16;
     Knobs knobs = a.knobs;
     KeyXf<K> xf = make_key_xf<K>(a.key_kind, a.descending);
+    uint32_t shape = uint32_t(sizeof(K)) | uint32_t(VB) << 8 | uint32_t(passes) << 16 | 2u << 24;
     void* args[] = {&k0, &k1, &v0, &v1, &n, &begin, &end, &np, &counts, &status, &gagg, &ginc,
-                    &tiles, &tiles_pad, &groups_pad, &zero_base, &zero_vec4, &ctrl, &knobs, &xf};
+                    &tiles, &tiles_pad, &groups_pad, &zero_base, &zero_vec4, &ctrl, &knobs, &xf,
+                    &shape};
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(THREADS);

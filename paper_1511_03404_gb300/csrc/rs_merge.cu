@@ -15,6 +15,7 @@
 #include <algorithm>
 
 #include "../../include/rs.h"
+#include "rs_debug.cuh"
 #include "rs_host.h"
 
 namespace rs {
@@ -172,6 +173,7 @@ __global__ void __launch_bounds__(kMsThreads) k_ms_tile(const K* src, const V* v
   }
   __syncthreads();
   for (uint32_t i = tid; i < len; i += kMsThreads) {
+    if (!dbg_ok(uint64_t(base) + i, n, kSiteMergeTile)) continue;
     dst[base + i] = sk[pad(i)];
     if constexpr (HAS_V) vdst[base + i] = sv[pad(i)];
   }
@@ -189,7 +191,8 @@ __global__ void k_ms_split(const K* __restrict__ src, uint32_t n, uint32_t w,
     const uint64_t base = p / (2ull * w) * (2ull * w);
     const uint32_t na = uint32_t(min(uint64_t(w), n - base));
     const uint32_t nb = uint32_t(n - base - na < w ? n - base - na : w);
-    split[c] = merge_path(src + base, na, src + base + na, nb, uint32_t(p - base));
+    const uint32_t at = merge_path(src + base, na, src + base + na, nb, uint32_t(p - base));
+    if (dbg_ok(c, tiles, kSiteMergeSplit)) split[c] = at;
   }
 }
 
@@ -250,6 +253,7 @@ __global__ void __launch_bounds__(kMsThreads) k_ms_merge(const K* __restrict__ s
   }
   __syncthreads();
   for (uint32_t t = tid; t < total; t += kMsThreads) {
+    if (!dbg_ok(p0 + t, n, kSiteMergeOut)) continue;
     dst[p0 + t] = sk[pad(t)];
     if constexpr (HAS_V) vdst[p0 + t] = sv[pad(t)];
   }

@@ -19,8 +19,10 @@ namespace {
 
 // Workspace of a sort of up to RS_NOALLOC_MAX_N keys: control block, digit
 // counts and offsets, one look-back word per (pass, tile, digit) and two per
-// (pass, group of tiles, digit): about 8.5 MiB at 2^23 keys.
-constexpr size_t kScratchBytes = size_t(9) << 20;
+// (pass, group of tiles, digit): about 8.5 MiB at 2^23 keys with 4096-key
+// tiles.  A tile shape whose workspace would not fit is not used here (see
+// pick_config).
+constexpr size_t kScratchBytes = RS_NOALLOC_SCRATCH_BYTES;
 
 __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
@@ -45,6 +47,28 @@ rs_status scratch_address(void** out) {
   return RS_OK;
 }
 
+// The configuration of a sort of n keys over [begin_bit, end_bit) whose
+// workspace fits the array: the library's own choice when it fits, else the
+// compiled variant with the smallest workspace for n (every variant gives the
+// same sorted result).  RS_ERR_INVALID when none fits.
+rs_status pick_config(size_t n, int begin_bit, int end_bit, rs_config* cfg) {
+  *cfg = rs_config{0, -1, RS_KEY_UNSIGNED, 0};
+  size_t need = 0;
+  rs_status st = rs_workspace_bytes(4, 0, n, begin_bit, end_bit, nullptr, &need);
+  if (st != RS_OK) return st;
+  if (need <= kScratchBytes) return RS_OK;
+  size_t best = ~size_t(0);
+  const int count = rs_num_variants(4, 0);
+  for (int i = 0; i < count; ++i) {
+    rs_config c{0, i, RS_KEY_UNSIGNED, 0};
+    if (rs_workspace_bytes(4, 0, n, begin_bit, end_bit, &c, &need) == RS_OK && need < best) {
+      best = need;
+      cfg->variant = i;
+    }
+  }
+  return best <= kScratchBytes ? RS_OK : RS_ERR_INVALID;
+}
+
 }  // namespace
 
 extern "C" {
@@ -54,15 +78,22 @@ rs_status rs_sort_keys_u32_noalloc(uint32_t* keys, uint32_t* keys_alt, size_t n,
   if (!result_in_alt) return RS_ERR_INVALID;
   *result_in_alt = 0;
   if (n > RS_NOALLOC_MAX_N) return RS_ERR_INVALID;
-  size_t need = 0;
-  const rs_status st = rs_workspace_bytes(4, 0, n, begin_bit, end_bit, nullptr, &need);
+  rs_config cfg;
+  const rs_status st = pick_config(n, begin_bit, end_bit, &cfg);
   if (st != RS_OK) return st;
-  if (need > kScratchBytes) return RS_ERR_INVALID;
   void* ws = nullptr;
   const rs_status ad = scratch_address(&ws);
   if (ad != RS_OK) return ad;
-  return rs_sort_keys_u32(keys, keys_alt, n, begin_bit, end_bit, ws, kScratchBytes, stream,
-                          result_in_alt);
+  return rs_sort(4, 0, keys, nullptr, keys_alt, nullptr, n, begin_bit, end_bit, &cfg, ws,
+                 kScratchBytes, stream, result_in_alt);
+}
+
+rs_status rs_sort_keys_u32_noalloc_status(rs_stream_t stream, uint32_t* info) {
+  if (info) *info = 0;
+  void* ws = nullptr;
+  const rs_status ad = scratch_address(&ws);
+  if (ad != RS_OK) return ad;
+  return rs_workspace_status(ws, stream, info);
 }
 
 }  // extern "C"

@@ -34,7 +34,7 @@ constexpr int kMaxSamples = 4096;
 __global__ void k_ss_block_offsets(uint64_t* off, uint64_t nblk, uint64_t n) {
   for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i <= nblk;
        i += uint64_t(gridDim.x) * blockDim.x)
-    off[i] = min(i * kSampleBlock, n);
+    if (dbg_ok(i, nblk + 1, kSiteSampleOff)) off[i] = min(i * kSampleBlock, n);
 }
 
 // sample[i * s + j] = block i's element floor(j * L_i / s).
@@ -45,7 +45,7 @@ __global__ void k_ss_sample(const uint32_t* __restrict__ keys, uint64_t n, uint3
     const uint64_t blk = t / s, j = t % s;
     const uint64_t base = blk * kSampleBlock;
     const uint64_t len = min(uint64_t(kSampleBlock), n - base);
-    sample[t] = keys[base + (j * len) / s];
+    if (dbg_ok(t, m, kSiteSampleSample)) sample[t] = keys[base + (j * len) / s];
   }
 }
 
@@ -54,7 +54,7 @@ __global__ void k_ss_splitters(const uint32_t* __restrict__ sorted, uint64_t m, 
                                uint32_t* __restrict__ spl) {
   for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q + 1 < buckets;
        q += gridDim.x * blockDim.x)
-    spl[q] = sorted[((uint64_t(q) + 1) * m) / buckets];
+    if (dbg_ok(q, buckets - 1u, kSiteSampleSplitter)) spl[q] = sorted[((uint64_t(q) + 1) * m) / buckets];
 }
 
 // Number of elements <= x in the sorted run a[0 .. len).
@@ -93,7 +93,8 @@ __global__ void __launch_bounds__(1024) k_ss_count(const uint32_t* __restrict__ 
   block_bounds(s_blk, len, spl, buckets, s_e);
   __syncthreads();
   for (uint32_t q = threadIdx.x; q < buckets; q += blockDim.x)
-    counts[uint64_t(q) * nblk + blk] = s_e[q] - (q ? s_e[q - 1] : 0u);
+    if (dbg_ok(uint64_t(q) * nblk + blk, uint64_t(buckets) * nblk, kSiteSampleCount))
+      counts[uint64_t(q) * nblk + blk] = s_e[q] - (q ? s_e[q - 1] : 0u);
 }
 
 // One CTA per block: element i of bucket q's run goes to
@@ -125,6 +126,7 @@ __global__ void __launch_bounds__(1024) k_ss_scatter(const uint32_t* __restrict_
     }
     const uint32_t q = lo;
     const uint64_t d = uint64_t(dest[uint64_t(q) * nblk + blk]) + (i - (q ? s_e[q - 1] : 0u));
+    if (!dbg_ok(d, n, kSiteSampleOut)) continue;
     kout[d] = s_blk[i];
     vout[d] = vals[base + i];
   }
@@ -192,7 +194,8 @@ __global__ void k_ss_bucket_offsets(const uint32_t* __restrict__ dest, uint64_t 
                                     uint32_t buckets, uint64_t n, uint64_t* __restrict__ off) {
   for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q <= buckets;
        q += gridDim.x * blockDim.x)
-    off[q] = q < buckets ? uint64_t(dest[uint64_t(q) * nblk]) : n;
+    if (dbg_ok(q, uint64_t(buckets) + 1, kSiteSampleBucket))
+      off[q] = q < buckets ? uint64_t(dest[uint64_t(q) * nblk]) : n;
 }
 
 struct SampleLayout {

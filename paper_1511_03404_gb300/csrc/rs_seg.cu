@@ -66,6 +66,7 @@ struct SegSort {
     a.offsets = reinterpret_cast<uint32_t*>(w + L.offsets);
     a.status = reinterpret_cast<uint32_t*>(w + L.status);
     a.tiles_max = L.tiles_max;
+    a.nseg = nseg;
     a.knobs = knobs;
     using V = ValT<VB>;
     const unsigned grid = unsigned(device_info().sms * occ);

@@ -119,7 +119,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     const uint32_t e_chunk = block_exclusive_scan<THREADS>(nc, s_tot);
     const uint32_t r_small = s_run[0], r_long = s_run[1], r_tile = s_run[2],
                    r_chunk = s_run[3];
-    if (small) small_ids[r_small + e_small] = uint32_t(s);
+    if (small && dbg_ok(r_small + e_small, nseg, kSiteSegPlan))
+      small_ids[r_small + e_small] = uint32_t(s);
     if (is_long) {
       const uint32_t li = r_long + e_long;
       SegDesc d;
@@ -129,7 +130,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       d.chunk0 = r_chunk + e_chunk;
       d.seg = uint32_t(s);
       d.pad[0] = d.pad[1] = 0u;
-      descs[li] = d;
+      if (dbg_ok(li, nseg, kSiteSegPlan)) descs[li] = d;
       if (uint64_t(d.tile0) + nt <= tiles_max && uint64_t(d.chunk0) + nc <= chunks_max) {
         for (uint32_t i = 0; i < nt; ++i) tile_seg[d.tile0 + i] = li;
         for (uint32_t i = 0; i < nc; ++i) chunk_seg[d.chunk0 + i] = li;
@@ -210,6 +211,7 @@ struct SegArgs {
   uint32_t* offsets;  // [nseg][passes][RADIX]
   uint32_t* status;   // [passes][tiles_max][RADIX]
   uint64_t tiles_max;
+  uint64_t nseg;      // segments (debug bounds checks)
   Knobs knobs;
 };
 
@@ -287,6 +289,7 @@ __device__ __forceinline__ void seg_cta_sort(const K* kin, const ValT<VB>* vin, 
     __syncthreads();
   }
   for (uint32_t i = tid; i < len; i += THREADS) {
+    if (!dbg_ok(i, len, kSiteSegSmallOut)) continue;
     kout[i] = s_k[i];
     if constexpr (VB > 0) vout[i] = s_v[i];
   }
@@ -380,7 +383,8 @@ __global__ void __launch_bounds__(THREADS, 2)
       uint32_t c = 0u;
 #pragma unroll
       for (int l = 0; l < SLOTS; ++l) c += row[(l + lane) & (SLOTS - 1)];  // rotated: no conflicts
-      if (c) atomicAdd(&cnt[w], c);
+      if (c && dbg_ok(uint64_t(li) * passes * RADIX + w, a.nseg * passes * RADIX, kSiteSegCounts))
+        atomicAdd(&cnt[w], c);
     }
     // clear the look-back words of this chunk's tiles, every pass
     const uint32_t t_first = lc * uint32_t(CHUNK_TILES);
@@ -389,7 +393,9 @@ __global__ void __launch_bounds__(THREADS, 2)
       uint32_t* st = a.status + size_t(p) * a.tiles_max * RADIX;
       const uint32_t nw = (t_last - t_first) * RADIX;
       for (uint32_t i = tid; i < nw; i += THREADS)
-        st[lb_index<RADIX>(d.tile0 + t_first + i / RADIX, i % RADIX)] = 0u;
+        if (dbg_ok(lb_index<RADIX>(d.tile0 + t_first + i / RADIX, i % RADIX),
+                   a.tiles_max * RADIX, kSiteSegClear))
+          st[lb_index<RADIX>(d.tile0 + t_first + i / RADIX, i % RADIX)] = 0u;
     }
     __syncthreads();
     uint32_t* state = a.state + size_t(li) * kSegStateWords;
@@ -398,7 +404,8 @@ __global__ void __launch_bounds__(THREADS, 2)
       // become visible before the ticket
       __threadfence();
       const uint32_t chunks = (d.len + CHUNK - 1) / CHUNK;
-      s_last = atomicAdd(&state[kSegTicket], 1u) == chunks - 1u;
+      s_last = dbg_ok(li, a.nseg, kSiteSegState) &&
+               atomicAdd(&state[kSegTicket], 1u) == chunks - 1u;
     }
     __syncthreads();
     if (s_last) {
@@ -409,7 +416,9 @@ __global__ void __launch_bounds__(THREADS, 2)
       for (int p = 0; p < passes; ++p) {
         const uint32_t c = tid < RADIX ? ld_relaxed(&cnt[p * RADIX + tid]) : 0u;
         const uint32_t e = block_exclusive_scan<THREADS>(c, s_tot);
-        if (tid < RADIX) offs[p * RADIX + tid] = e;
+        if (tid < RADIX && dbg_ok(uint64_t(li) * passes * RADIX + p * RADIX + tid,
+                                  a.nseg * passes * RADIX, kSiteSegCounts))
+          offs[p * RADIX + tid] = e;
         if (!__syncthreads_or(tid < RADIX && c == d.len)) exec |= 1u << p;
       }
       if (tid == 0) {
@@ -499,7 +508,10 @@ __global__ void __launch_bounds__(THREADS, 4)
       t.gagg = nullptr;  // segments are short: flat walk
       t.ginc = nullptr;
       t.tiles = ntiles;
+      t.lb_words = a.tiles_max * RADIX;
+      t.g_words = 0;
       t.silent = false;
+      t.dbg_bad = false;
       t.trace = nullptr;
       t.lb_small = false;
       t.xf = KeyXf<K>{};
@@ -511,7 +523,7 @@ __global__ void __launch_bounds__(THREADS, 4)
     __syncthreads();
     if (tid == 0) {
       __threadfence();  // the tile's output, ordered before by the barrier, then the count
-      atomicAdd(&state[kSegDone0 + p], 1u);
+      if (dbg_ok(li, a.nseg, kSiteSegState)) atomicAdd(&state[kSegDone0 + p], 1u);
     }
     __syncthreads();
   }

@@ -35,7 +35,7 @@ RS_KERNEL_KINDS = 6
 KERNEL_NAMES = ("upsweep", "onesweep", "small", "segmented", "merge", "sample")
 
 (RS_DEBUG_TIMEOUT_NS, RS_DEBUG_DROP_PUBLISH_TILE, RS_DEBUG_DROP_PUBLISH_PASS, RS_DEBUG_TRACE_PTR,
- RS_DEBUG_TRACE_TILES, RS_DEBUG_TRACE_PASS, RS_DEBUG_LB_SMALL) = range(7)
+ RS_DEBUG_TRACE_TILES, RS_DEBUG_TRACE_PASS, RS_DEBUG_LB_SMALL, RS_DEBUG_BAD_INDEX_TILE) = range(8)
 
 
 class RsError(RuntimeError):
@@ -74,6 +74,15 @@ class rs_server_config(ctypes.Structure):
                 ("large_low_priority", ctypes.c_int)]
 
 
+class rs_sort_stats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("info", ctypes.c_uint32), ("form", ctypes.c_int),
+                ("key_bytes", ctypes.c_int), ("val_bytes", ctypes.c_int),
+                ("passes", ctypes.c_int), ("n", ctypes.c_uint64),
+                ("moved_mask", ctypes.c_uint32), ("skipped_mask", ctypes.c_uint32),
+                ("upsweep_ms", ctypes.c_double), ("pass_ms", ctypes.c_double * 16),
+                ("total_ms", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
 class rs_trace_record(ctypes.Structure):
     _fields_ = [("submit_s", ctypes.c_double), ("admit_s", ctypes.c_double),
                 ("done_s", ctypes.c_double), ("n", ctypes.c_uint64),
@@ -96,6 +105,10 @@ _SIGS = {
     "rs_sort_pairs_u32": ([_vp, _vp, _vp, _vp, _sz, _i, _i, _vp, _sz, _vp, _vp], _i),
     "rs_sort_pairs_u64": ([_vp, _vp, _vp, _vp, _sz, _i, _i, _vp, _sz, _vp, _vp], _i),
     "rs_sort_keys_u32_noalloc": ([_vp, _vp, _sz, _i, _i, _vp, _vp], _i),
+    "rs_sort_keys_u32_noalloc_status": ([_vp, _vp], _i),
+    "rs_sort_host": ([_i, _i, _vp, _vp, _vp, _vp, _sz, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp, _sz,
+                      _vp, _vp], _i),
+    "rs_workspace_stats": ([_vp, _vp, _vp], _i),
     "rs_sort": ([_i, _i, _vp, _vp, _vp, _vp, _sz, _i, _i, _vp, _vp, _sz, _vp, _vp], _i),
     "rs_digit_counts": ([_i, _vp, _sz, _i, _i, _i, _vp, _vp, _vp, _vp, _sz, _vp], _i),
     "rs_workspace_status": ([_vp, _vp, _vp], _i),
@@ -124,19 +137,26 @@ _SIGS = {
     "rs_profile_begin": ([_i], _i),
     "rs_profile_end": ([_vp, _vp, _vp], _i),
     "rs_debug_set": ([_i, ctypes.c_longlong], _i),
+    "rs_debug_status": ([_vp, _vp, _vp], _i),
 }
 
 
+def debug_library() -> bool:
+    """Whether this process uses the debug build (RS_LIBRARY=debug)."""
+    return os.environ.get("RS_LIBRARY", "") == "debug"
+
+
 def library_path() -> str:
-    return _build.LIB_PATH
+    return _build.DEBUG_LIB_PATH if debug_library() else _build.LIB_PATH
 
 
 def load():
-    """Build (if needed) and load librs.so; raises if that is impossible."""
+    """Build (if needed) and load librs.so (librs_debug.so when the
+    environment sets RS_LIBRARY=debug); raises if that is impossible."""
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.build()
+            path = _build.build(debug=debug_library())
             lib = ctypes.CDLL(path, mode=ctypes.RTLD_GLOBAL)
             for name, (args, res) in _SIGS.items():
                 if not hasattr(lib, name):
@@ -253,6 +273,7 @@ def rs_sort_pairs_u64(keys, vals, keys_alt, vals_alt, n, begin_bit, end_bit, ws,
 
 
 RS_NOALLOC_MAX_N = 1 << 23
+RS_NOALLOC_SCRATCH_BYTES = 9 << 20
 
 
 def rs_sort_keys_u32_noalloc(keys, keys_alt, n, begin_bit, end_bit, stream):
@@ -260,6 +281,32 @@ def rs_sort_keys_u32_noalloc(keys, keys_alt, n, begin_bit, end_bit, stream):
     st = load().rs_sort_keys_u32_noalloc(keys, keys_alt, n, begin_bit, end_bit, stream,
                                          ctypes.byref(r))
     return st, r.value
+
+
+def rs_sort_keys_u32_noalloc_status(stream):
+    info = ctypes.c_uint32()
+    st = load().rs_sort_keys_u32_noalloc_status(stream, ctypes.byref(info))
+    return st, info.value
+
+
+def rs_sort_host(key_bytes, val_bytes, h_keys, h_vals, h_out_keys, h_out_vals, n, begin_bit,
+                 end_bit, keys, vals, keys_alt, vals_alt, ws, ws_bytes, stream, radix_bits=0,
+                 variant=-1, key_kind=RS_KEY_UNSIGNED, descending=False):
+    r = _out_int()
+    st = load().rs_sort_host(key_bytes, val_bytes, h_keys, h_vals, h_out_keys, h_out_vals, n,
+                             begin_bit, end_bit, _cfg(radix_bits, variant, key_kind, descending),
+                             keys, vals, keys_alt, vals_alt, ws, ws_bytes, stream,
+                             ctypes.byref(r))
+    return st, r.value
+
+
+def rs_workspace_stats(ws, stream):
+    """(status, dict) with the fields of rs_sort_stats; pass_ms as a list of `passes` floats."""
+    out = rs_sort_stats()
+    st = load().rs_workspace_stats(ws, stream, ctypes.byref(out))
+    d = {name: getattr(out, name) for name, _ in rs_sort_stats._fields_}
+    d["pass_ms"] = list(out.pass_ms)[:max(0, out.passes)]
+    return st, d
 
 
 def rs_sort(key_bytes, val_bytes, keys, vals, keys_alt, vals_alt, n, begin_bit, end_bit, ws,
@@ -418,6 +465,13 @@ def rs_profile_end():
     st = load().rs_profile_end(launches, ms, by)
     return st, {KERNEL_NAMES[k]: {"launches": launches[k], "ms": ms[k], "bytes": by[k]}
                 for k in range(RS_KERNEL_KINDS)}
+
+
+def rs_debug_status():
+    """(status, debug_build, site, index) of the bounds checks of a debug build."""
+    dbg, site, index = ctypes.c_int(), ctypes.c_uint32(), ctypes.c_uint64()
+    st = load().rs_debug_status(ctypes.byref(dbg), ctypes.byref(site), ctypes.byref(index))
+    return st, bool(dbg.value), site.value, index.value
 
 
 def rs_debug_set(knob: int, value: int) -> int:

@@ -120,3 +120,47 @@ def test_server_entry_points_reject_null_without_gpu():
     assert lib.rs_server_completed(None, None, 0, ctypes.byref(out)) == rs.RS_ERR_INVALID
     assert lib.rs_server_stats(None, None) == rs.RS_ERR_INVALID
     assert lib.rs_poll(None, 1, None) == rs.RS_ERR_INVALID
+
+
+def test_noalloc_array_fits_a_compiled_shape_at_every_size():
+    """rs_sort_keys_u32_noalloc takes the tuned shape when its workspace fits
+    the library's fixed array, else the shape with the smallest workspace:
+    some shape must fit at every accepted size, whatever the tuned table says."""
+    count = rs.rs_num_variants(4, 0)
+    for n in (2, 4097, 65537, 1 << 20, (1 << 22) + 3, rs.RS_NOALLOC_MAX_N):
+        sizes = [rs.rs_workspace_bytes(4, 0, n, 0, 32, variant=i)[1] for i in range(count)
+                 if rs.rs_variant_info(4, 0, i)["max_n"] >= n]
+        assert sizes and min(sizes) <= rs.RS_NOALLOC_SCRATCH_BYTES, n
+
+
+def test_host_buffer_sort_checks_arguments_before_enqueuing():
+    fake = 1 << 40  # never dereferenced: every call below fails its host checks
+    h = 1 << 41
+    # wrong type combination
+    assert rs.rs_sort_host(4, 8, h, h, h, h, 100, 0, 32, fake, fake + 4096, fake + 8192,
+                           fake + 12288, None, 0, None)[0] == rs.RS_ERR_INVALID
+    # host values without a value type, and a missing host output
+    assert rs.rs_sort_host(4, 0, h, h, h, None, 100, 0, 32, fake, None, fake + 4096, None, None,
+                           0, None)[0] == rs.RS_ERR_INVALID
+    assert rs.rs_sort_host(4, 0, h, None, None, None, 100, 0, 32, fake, None, fake + 4096, None,
+                           None, 0, None)[0] == rs.RS_ERR_INVALID
+    # same key buffer twice, bad bit range, too many elements
+    assert rs.rs_sort_host(4, 0, h, None, h, None, 100, 0, 32, fake, None, fake, None, None, 0,
+                           None)[0] == rs.RS_ERR_INVALID
+    assert rs.rs_sort_host(4, 0, h, None, h, None, 100, 0, 40, fake, None, fake + 4096, None,
+                           None, 0, None)[0] == rs.RS_ERR_INVALID
+    assert rs.rs_sort_host(4, 0, h, None, h, None, rs.RS_MAX_N + 1, 0, 32, fake, None,
+                           fake + 2**33, None, None, 0, None)[0] == rs.RS_ERR_INVALID
+    # misaligned keys, a bad key order
+    assert rs.rs_sort_host(8, 0, h, None, h, None, 100, 0, 64, fake + 4, None, fake + 4096, None,
+                           None, 0, None)[0] == rs.RS_ERR_INVALID
+    assert rs.rs_sort_host(4, 0, h, None, h, None, 100, 0, 32, fake, None, fake + 4096, None,
+                           None, 0, None, key_kind=7)[0] == rs.RS_ERR_INVALID
+    # missing workspace for a multi-CTA sort
+    assert rs.rs_sort_host(4, 0, h, None, h, None, 2**20, 0, 32, fake, None, fake + 2**30, None,
+                           None, 0, None)[0] == rs.RS_ERR_WORKSPACE
+
+
+def test_stats_entry_rejects_null_output():
+    lib = rs.load()
+    assert lib.rs_workspace_stats(None, None, None) == rs.RS_ERR_INVALID

@@ -1,6 +1,8 @@
 """Parity at the benchmark's full sizes, in the configuration bench.py times
 (the C ABI, the tuned variant choice): u32 pairs at n = 2^26 for the six
-distributions, u64 keys and u64 pairs at n = 2^27.  The oracle takes minutes
+distributions, u64 keys and u64 pairs at n = 2^27 for the six and 16-bit
+entropy keys, and the batched segmented workload (20,000 segments, about
+1.5e9 pairs).  The oracle takes minutes
 at these sizes, so the result is checked on the device by properties that
 together define the stable sort uniquely (values are the input positions):
 
@@ -15,7 +17,8 @@ import numpy as np
 import pytest
 
 import inputs
-from gpu_util import to_dev
+import oracle
+from gpu_util import from_dev, to_dev
 
 torch = pytest.importorskip("torch")
 
@@ -74,7 +77,7 @@ def test_u32_pairs_2p26(dist):
     check_pairs(src, out_k, out_v)
 
 
-@pytest.mark.parametrize("dist", ["uniform", "gaussian", "entropy16"])
+@pytest.mark.parametrize("dist", list(inputs.PAPER_DISTS) + ["entropy16"])
 def test_u64_keys_2p27(dist):
     k = inputs.keys(np.uint64, dist, 1 << 27)
     src, out_k, _ = run(8, 0, k)
@@ -82,7 +85,7 @@ def test_u64_keys_2p27(dist):
     assert bool((out_k == want).all())
 
 
-@pytest.mark.parametrize("dist", ["uniform", "entropy16"])
+@pytest.mark.parametrize("dist", list(inputs.PAPER_DISTS) + ["entropy16"])
 def test_u64_pairs_2p27(dist):
     k = inputs.keys(np.uint64, dist, 1 << 27)
     src, out_k, out_v = run(8, 8, k)
@@ -101,3 +104,70 @@ def test_largest_array(vb):
     else:
         want = ordered(torch.sort(ordered(src)).values)
         assert bool((out_k == want).all())
+
+
+def check_segmented(src, out_k, out_v, off):
+    """Every segment of the batched sort sorted stably, on the device.  The
+    values are the input positions 0 .. n-1, so the four properties of
+    check_pairs taken per segment fix the result uniquely: keys
+    non-decreasing inside each segment, the values a permutation of 0 .. n-1
+    in which every value stays inside its own position's segment, every
+    output key equal to the input key at its value, and equal keys of a
+    segment in increasing value order."""
+    n = src.numel()
+    dev = src.device
+    lengths = torch.from_numpy(np.diff(off).astype(np.int64)).to(dev)
+    seg = torch.repeat_interleave(torch.arange(lengths.numel(), dtype=torch.int32, device=dev),
+                                  lengths, output_size=n)
+    same = seg[1:] == seg[:-1]
+    o = ordered(out_k)
+    assert bool(((o[1:] >= o[:-1]) | ~same).all()), "a segment is not sorted"
+    idx = out_v.long()
+    assert int(idx.min()) == 0 and int(idx.max()) == n - 1
+    seen = torch.zeros(n, dtype=torch.uint8, device=dev)
+    seen[idx] = 1
+    assert bool(seen.bool().all()), "values are not a permutation"
+    del seen
+    assert bool((seg[idx] == seg).all()), "a value left its segment"
+    assert bool((src[idx] == out_k).all()), "a key left its value"
+    eq = (o[1:] == o[:-1]) & same
+    assert bool(((idx[1:] > idx[:-1]) | ~eq).all()), "equal keys out of input order"
+
+
+def test_segmented_twenty_thousand_segments_full_size():
+    """The batched workload itself: 20,000 segments, lengths log-uniform in
+    [1, 2^20] (seed 1), about 1.5e9 u32 pairs in all -- more elements than
+    RS_MAX_N and byte offsets beyond 2^32.  Checked on the device as a whole
+    (check_segmented), and against the oracle on sampled segments: the last
+    ones (the largest offsets), the longest ones and random ones."""
+    L = inputs.segment_lengths(20000, seed=1, max_log2=20)
+    off = inputs.offsets_from_lengths(L)
+    n = int(off[-1])
+    assert n > rs.RS_MAX_N and 4 * n > 2**32
+    k = inputs.keys(np.uint32, "uniform", n, seed=1)
+    dk = to_dev(k, torch)
+    src = dk.clone()
+    dv = torch.arange(n, dtype=torch.int32, device="cuda")
+    ka, va = torch.empty_like(dk), torch.empty_like(dv)
+    doff = to_dev(off.astype(np.uint64), torch)
+    st, need = rs.rs_segmented_workspace_bytes(n, len(L), 0, 32)
+    rs.check(st, "rs_segmented_workspace_bytes")
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    h = torch.cuda.current_stream().cuda_stream
+    st, in_alt = rs.rs_segmented_sort_pairs(dk.data_ptr(), dv.data_ptr(), ka.data_ptr(),
+                                            va.data_ptr(), n, doff.data_ptr(), len(L), 0, 32,
+                                            ws.data_ptr(), ws.numel(), h)
+    rs.check(st, "rs_segmented_sort_pairs")
+    rs.check(rs.rs_workspace_status(ws.data_ptr(), h)[0], "device status")
+    out_k, out_v = (ka, va) if in_alt else (dk, dv)
+    del ws
+    check_segmented(src, out_k, out_v, off)
+    rng = np.random.default_rng(3)
+    picks = set(range(len(L) - 40, len(L)))
+    picks |= set(np.argsort(L, kind="stable")[-20:].tolist())
+    picks |= set(rng.choice(len(L), 200, replace=False).tolist())
+    for s in sorted(picks):
+        a, b = int(off[s]), int(off[s + 1])
+        ek, ev = oracle.lsd_sort(k[a:b], np.arange(a, b, dtype=np.uint32))
+        assert np.array_equal(from_dev(out_k[a:b], np.uint32), ek), s
+        assert np.array_equal(from_dev(out_v[a:b], np.uint32), ev), s

@@ -1,6 +1,6 @@
-"""Named, timed workloads of the library's other entry points: merge sort
-(Sec. 2.4), the sample-sort partition (Sec. 2.7) and the batched segmented
-sort, on seeded uniform keys.
+"""Named, timed workloads of the library's entry points: the LSD sort of any
+key type (Sec. 2.6), merge sort (Sec. 2.4), the sample-sort partition
+(Sec. 2.7) and the batched segmented sort, on seeded keys.
 
 Each function runs its entry point on the device, times it with CUDA events
 on the launching stream (the input restored outside the events, L2 flushed
@@ -189,15 +189,73 @@ def segmented(n: int = 1 << 24, nseg: int = 1000, reps: int = 5, peak_gbs=None,
             "bytes": "histograms 4 n, then 2 n (4 + 4) per pass"}
 
 
+def sort(n: int = 1 << 26, key_bytes: int = 4, val_bytes: int = 4, dist: str = "uniform",
+         variant: int = -1, reps: int = 5, peak_gbs=None, device: int = 0) -> dict:
+    """One LSD sort (rs_sort) of n seeded keys of `dist` (values = index when
+    val_bytes > 0), with the library's tile shape unless `variant` names one:
+    the sort time, each kernel kind's rate, and the per-pass device times and
+    moved / skipped passes of the last call (rs_workspace_stats)."""
+    import torch
+    _uniform_u32(1)  # puts the input generators on the path
+    import inputs
+    dev = torch.device("cuda", device)
+    stream = torch.cuda.Stream(dev)
+    dt, sdt = (np.uint32, torch.int32) if key_bytes == 4 else (np.uint64, torch.int64)
+    keys0 = torch.from_numpy(inputs.keys(dt, dist, n).view(np.int32 if key_bytes == 4
+                                                            else np.int64)).to(dev)
+    k, ka = torch.empty_like(keys0), torch.empty_like(keys0)
+    vals0 = torch.arange(n, dtype=sdt, device=dev) if val_bytes else None
+    v = torch.empty_like(keys0) if val_bytes else None
+    va = torch.empty_like(keys0) if val_bytes else None
+    st, need = rs.rs_workspace_bytes(key_bytes, val_bytes, n, 0, 8 * key_bytes, variant=variant)
+    rs.check(st, "rs_workspace_bytes")
+    ws = torch.empty(max(need, 256), dtype=torch.uint8, device=dev)
+    ptr = lambda t: None if t is None else t.data_ptr()  # noqa: E731
+
+    def restore():
+        with torch.cuda.stream(stream):
+            k.copy_(keys0)
+            if val_bytes:
+                v.copy_(vals0)
+
+    def call():
+        st_, _ = rs.rs_sort(key_bytes, val_bytes, ptr(k), ptr(v), ptr(ka), ptr(va), n, 0,
+                            8 * key_bytes, ws.data_ptr(), ws.numel(), stream.cuda_stream,
+                            variant=variant)
+        rs.check(st_, "rs_sort")
+
+    ms, prof = _timed(torch, stream, restore, call, reps)
+    st, stats = rs.rs_workspace_stats(ws.data_ptr(), stream.cuda_stream)
+    rs.check(st, "rs_workspace_stats")
+    rs.check(stats["status"], "device status")
+    return {"workload": f"LSD sort, {8 * key_bytes}-bit keys" +
+                        (f" + {8 * val_bytes}-bit values" if val_bytes else "") +
+                        f", n={n}, {dist} (mt19937 seed 1), variant {variant}",
+            "ms": ms, "gkeys_per_s": n / (ms / 1e3) / 1e9,
+            "upsweep": _kernel_rate(prof["upsweep"], peak_gbs),
+            "passes": _kernel_rate(prof["onesweep"], peak_gbs),
+            "pass_ms": [round(t, 4) for t in stats["pass_ms"]],
+            "upsweep_ms": round(stats["upsweep_ms"], 4),
+            "moved_mask": stats["moved_mask"], "skipped_mask": stats["skipped_mask"],
+            "bytes": "upsweep n K; each moving pass 2 n (K + V)"}
+
+
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser(description="run one named workload and print its timing")
-    ap.add_argument("workload", choices=("merge", "merge_pairs", "sample_partition", "segmented"))
+    ap.add_argument("workload", choices=("sort", "merge", "merge_pairs", "sample_partition",
+                                         "segmented"))
     ap.add_argument("--n", type=int, default=1 << 26)
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--buckets", type=int, default=64)
+    ap.add_argument("--key-bytes", type=int, default=4, choices=(4, 8))
+    ap.add_argument("--val-bytes", type=int, default=4, choices=(0, 4, 8))
+    ap.add_argument("--dist", default="uniform")
+    ap.add_argument("--variant", type=int, default=-1)
     args = ap.parse_args(argv)
     rs.load()
-    if args.workload == "merge":
+    if args.workload == "sort":
+        r = sort(args.n, args.key_bytes, args.val_bytes, args.dist, args.variant, args.reps)
+    elif args.workload == "merge":
         r = merge(args.n, 4, 0, args.reps)
     elif args.workload == "merge_pairs":
         r = merge(args.n, 4, 4, args.reps)

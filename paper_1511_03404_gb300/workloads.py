@@ -149,16 +149,19 @@ def sample_partition(n: int = 1 << 26, samples: int = 64, buckets: int = 64, rep
 
 
 def segmented(n: int = 1 << 24, nseg: int = 1000, reps: int = 5, peak_gbs=None,
-              device: int = 0) -> dict:
+              device: int = 0, stated: bool = False) -> dict:
     """Batched segmented sort of u32 pairs (values = index): nseg segments of
-    log-uniform lengths in [1, 2^20] (seed 1) scaled to n elements in all,
-    through ``rs_segmented_sort_pairs``."""
+    log-uniform lengths in [1, 2^20] (seed 1) scaled to n elements in all
+    (stated: the lengths as drawn, not scaled; n is then ignored), through
+    ``rs_segmented_sort_pairs``."""
     import torch
     _uniform_u32(1)  # puts the input generators on the path
     import inputs
     dev = torch.device("cuda", device)
     stream = torch.cuda.Stream(dev)
-    lengths = inputs.scale_lengths(inputs.segment_lengths(nseg, seed=1, max_log2=20), n)
+    lengths = inputs.segment_lengths(nseg, seed=1, max_log2=20)
+    if not stated:
+        lengths = inputs.scale_lengths(lengths, n)
     off = inputs.offsets_from_lengths(lengths)
     total = int(off[-1])
     keys0 = torch.from_numpy(_uniform_u32(total).view(np.int32)).to(dev)
@@ -182,8 +185,9 @@ def segmented(n: int = 1 << 24, nseg: int = 1000, reps: int = 5, peak_gbs=None,
         rs.check(st_, "rs_segmented_sort_pairs")
 
     ms, prof = _timed(torch, stream, restore, call, reps)
-    return {"workload": f"segmented sort, u32 pairs, {len(lengths)} log-uniform segments scaled "
-                        f"to n={total}, uniform keys (mt19937 seed 1)",
+    law = "as drawn" if stated else "scaled"
+    return {"workload": f"segmented sort, u32 pairs, {len(lengths)} log-uniform segments ({law}), "
+                        f"n={total}, uniform keys (mt19937 seed 1)",
             "ms": ms, "gkeys_per_s": total / (ms / 1e3) / 1e9,
             "kernels": _kernel_rate(prof["segmented"], peak_gbs),
             "bytes": "histograms 4 n, then 2 n (4 + 4) per pass"}
@@ -251,6 +255,10 @@ def main(argv=None) -> int:
     ap.add_argument("--val-bytes", type=int, default=4, choices=(0, 4, 8))
     ap.add_argument("--dist", default="uniform")
     ap.add_argument("--variant", type=int, default=-1)
+    ap.add_argument("--segments", type=int, default=1000)
+    ap.add_argument("--stated", action="store_true",
+                    help="segmented: the log-uniform lengths as drawn (20,000 segments: about "
+                         "1.5e9 pairs), not scaled to --n")
     args = ap.parse_args(argv)
     rs.load()
     if args.workload == "sort":
@@ -260,7 +268,7 @@ def main(argv=None) -> int:
     elif args.workload == "merge_pairs":
         r = merge(args.n, 4, 4, args.reps)
     elif args.workload == "segmented":
-        r = segmented(args.n, 1000, args.reps)
+        r = segmented(args.n, args.segments, args.reps, stated=args.stated)
     else:
         r = sample_partition(args.n, args.buckets, args.buckets, args.reps)
     print(json.dumps(r))

@@ -34,7 +34,7 @@ struct SegSort {
     k_seg_plan<PLAN_THREADS><<<1, PLAN_THREADS, 0, s>>>(
         d_off, nseg, n, uint32_t(C::SMALL_TILE), uint32_t(C::TILE), uint32_t(C::CHUNK), ctrl,
         reinterpret_cast<uint32_t*>(w + L.small_ids), reinterpret_cast<SegDesc*>(w + L.descs),
-        reinterpret_cast<uint32_t*>(w + L.tile_seg), reinterpret_cast<uint32_t*>(w + L.chunk_seg),
+        reinterpret_cast<uint32_t*>(w + L.chunk_seg),
         L.tiles_max, L.chunks_max);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -59,7 +59,7 @@ struct SegSort {
     a.ctrl = ctrl;
     a.small_ids = reinterpret_cast<const uint32_t*>(w + L.small_ids);
     a.descs = reinterpret_cast<const SegDesc*>(w + L.descs);
-    a.tile_seg = reinterpret_cast<const uint32_t*>(w + L.tile_seg);
+    a.tdesc = reinterpret_cast<TileDesc*>(w + L.tdesc);
     a.chunk_seg = reinterpret_cast<const uint32_t*>(w + L.chunk_seg);
     a.state = reinterpret_cast<uint32_t*>(w + L.state);
     a.counts = reinterpret_cast<uint32_t*>(w + L.counts);

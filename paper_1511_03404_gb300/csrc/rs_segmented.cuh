@@ -4,20 +4,23 @@
 //
 //   k_seg_plan        one CTA: classifies segments (short ones fit one CTA,
 //                     long ones are tiled), numbers the work items and maps
-//                     every histogram chunk and pass tile to its segment.
+//                     every histogram chunk to its segment.
 //   k_seg_small       short segments, each sorted whole in one CTA's shared
 //                     memory (every pass), grid-stride over the short list;
+//   k_seg_hist        the digit histograms of the long segments, chunk by
+//                     chunk; each segment's last chunk scans them and writes
+//                     the descriptors of the segment's pass tiles;
 //   k_seg_persistent  SMs x resident CTAs, each looping over one global work
 //                     queue (an atomic counter) in this order:
-//                       [histogram chunks of long segments]
 //                       [pass 0 tiles of long segments] ... [pass P-1 tiles]
 //                     (kept apart from the short segments so that it needs
 //                     few registers and four CTAs fit on an SM)
-//                     A tile of pass p waits (bounded) until its segment's
-//                     histograms are scanned and, for p > 0, until every tile
-//                     of pass p-1 of its segment is written.  Every wait is on
-//                     items taken from the queue earlier, which are held by
-//                     running CTAs, so the queue always makes progress.
+//                     A tile reads its descriptor (written by the histogram
+//                     kernel, launched before); a tile of pass p > 0 waits
+//                     (bounded) until every tile of pass p-1 of its segment is
+//                     written.  Every wait is on items taken from the queue
+//                     earlier, which are held by running CTAs, so the queue
+//                     always makes progress.
 #pragma once
 
 #include "rs_kernels.cuh"
@@ -36,8 +39,23 @@ struct SegDesc {
 };
 static_assert(sizeof(SegDesc) == 32, "SegDesc is 32 bytes");
 
+// Everything a pass tile needs to start, in one 32-byte read: written for
+// every tile of a long segment by the segment's last histogram chunk, so the
+// tile needs no dependent read of a tile map, a segment descriptor and the
+// segment's state before it can load its keys.
+struct TileDesc {
+  uint64_t off;    // the segment's first element
+  uint32_t len;    // the segment's elements
+  uint32_t li;     // long-segment index (state, counts, offsets)
+  uint32_t tile0;  // the segment's first global pass tile
+  uint32_t exec;   // passes of the segment that move data (after the parity rule)
+  uint32_t pad[2];
+};
+static_assert(sizeof(TileDesc) == 32, "TileDesc is 32 bytes");
+
 // Per long segment: histogram ticket, ready word (bit 0: the histograms are
-// scanned; bits 1..: the mask of passes that move data), done counters.
+// scanned; bits 1..: the mask of passes that move data; kept for inspection,
+// the pass kernel takes the mask from its tile descriptor), done counters.
 constexpr int kSegStateWords = 16;
 enum SegStateField { kSegTicket = 0, kSegReady = 1, kSegDone0 = 3 };
 
@@ -52,7 +70,7 @@ enum SegCtrlField {
 };
 
 struct SegLayout {
-  size_t small_ids, descs, tile_seg, chunk_seg, state, counts, offsets, status, total;
+  size_t small_ids, descs, tdesc, chunk_seg, state, counts, offsets, status, total;
   size_t memset_bytes;  // Ctrl + state + counts
   size_t tiles_max, chunks_max;
 };
@@ -69,8 +87,8 @@ inline SegLayout seg_layout(size_t n, size_t nseg, int passes, int radix_bits, i
   L.offsets = L.memset_bytes;
   L.small_ids = align_up(L.offsets + nseg * passes * radix * 4, 256);
   L.descs = align_up(L.small_ids + nseg * 4, 256);
-  L.tile_seg = align_up(L.descs + nseg * sizeof(SegDesc), 256);
-  L.chunk_seg = align_up(L.tile_seg + L.tiles_max * 4, 256);
+  L.tdesc = align_up(L.descs + nseg * sizeof(SegDesc), 256);
+  L.chunk_seg = align_up(L.tdesc + L.tiles_max * sizeof(TileDesc), 256);
   L.status = align_up(L.chunk_seg + L.chunks_max * 4, 256);
   L.total = align_up(L.status + size_t(passes) * L.tiles_max * radix * 4, 256);
   return L;
@@ -82,7 +100,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     k_seg_plan(const uint64_t* __restrict__ off, uint64_t nseg, uint64_t n, uint32_t small_max,
                uint32_t tile, uint32_t chunk, Ctrl* __restrict__ ctrl,
                uint32_t* __restrict__ small_ids, SegDesc* __restrict__ descs,
-               uint32_t* __restrict__ tile_seg, uint32_t* __restrict__ chunk_seg,
+               uint32_t* __restrict__ chunk_seg,
                uint64_t tiles_max, uint64_t chunks_max) {
   __shared__ uint32_t s_tot[32];
   __shared__ uint32_t s_run[4];
@@ -121,8 +139,9 @@ __global__ void __launch_bounds__(THREADS, 1)
                    r_chunk = s_run[3];
     if (small && dbg_ok(r_small + e_small, nseg, kSiteSegPlan))
       small_ids[r_small + e_small] = uint32_t(s);
+    const uint32_t li = r_long + e_long;
+    bool map_ok = false;
     if (is_long) {
-      const uint32_t li = r_long + e_long;
       SegDesc d;
       d.off = off[s];
       d.len = uint32_t(len);
@@ -131,11 +150,21 @@ __global__ void __launch_bounds__(THREADS, 1)
       d.seg = uint32_t(s);
       d.pad[0] = d.pad[1] = 0u;
       if (dbg_ok(li, nseg, kSiteSegPlan)) descs[li] = d;
-      if (uint64_t(d.tile0) + nt <= tiles_max && uint64_t(d.chunk0) + nc <= chunks_max) {
-        for (uint32_t i = 0; i < nt; ++i) tile_seg[d.tile0 + i] = li;
-        for (uint32_t i = 0; i < nc; ++i) chunk_seg[d.chunk0 + i] = li;
-      } else {
-        s_bad = 1;
+      map_ok = uint64_t(d.tile0) + nt <= tiles_max && uint64_t(d.chunk0) + nc <= chunks_max;
+      if (!map_ok) s_bad = 1;
+    }
+    // the chunk map of these long segments: each warp writes its lanes'
+    // segments one after another, 32 consecutive entries per store (one
+    // thread writing its own segment's entries issued one store each)
+    {
+      const int lane = tid & 31;
+      const uint32_t c0 = r_chunk + e_chunk;
+      for (uint32_t m = __ballot_sync(kFull, map_ok); m != 0u; m &= m - 1u) {
+        const int src = __ffs(int(m)) - 1;
+        const uint32_t sli = __shfl_sync(kFull, li, src), sc0 = __shfl_sync(kFull, c0, src);
+        const uint32_t snc = __shfl_sync(kFull, nc, src);
+        for (uint32_t i = uint32_t(lane); i < snc; i += 32)
+          if (dbg_ok(uint64_t(sc0) + i, chunks_max, kSiteSegPlan)) chunk_seg[sc0 + i] = sli;
       }
     }
     __syncthreads();
@@ -204,7 +233,7 @@ struct SegArgs {
   Ctrl* ctrl;
   const uint32_t* small_ids;
   const SegDesc* descs;
-  const uint32_t* tile_seg;
+  TileDesc* tdesc;    // [tiles_max]
   const uint32_t* chunk_seg;
   uint32_t* state;    // [nseg][kSegStateWords]
   uint32_t* counts;   // [nseg][passes][RADIX]
@@ -369,11 +398,24 @@ __global__ void __launch_bounds__(THREADS, 2)
     if (uint32_t(tid) < head) count_key(keys[tid]);
     if (uint32_t(tid) < len - tail) count_key(keys[tail + tid]);
     const uint4* vp = reinterpret_cast<const uint4*>(keys + head);
-    for (uint32_t i = tid; i < nvec; i += THREADS) {
-      const uint4 v = vp[i];
-      const K* ks = reinterpret_cast<const K*>(&v);
+    // two 16-byte loads in flight per thread before their keys are counted
+    // (four need more than the 32 registers two CTAs of 1024 threads leave)
+    constexpr int UNROLL = 2;
+    for (uint32_t i0 = tid; i0 < nvec; i0 += THREADS * UNROLL) {
+      uint4 buf[UNROLL];
 #pragma unroll
-      for (int e = 0; e < VEC; ++e) count_key(ks[e]);
+      for (int u = 0; u < UNROLL; ++u) {
+        const uint32_t i = i0 + uint32_t(u) * THREADS;
+        if (i < nvec) buf[u] = vp[i];
+      }
+#pragma unroll
+      for (int u = 0; u < UNROLL; ++u) {
+        if (i0 + uint32_t(u) * THREADS < nvec) {
+          const K* ks = reinterpret_cast<const K*>(&buf[u]);
+#pragma unroll
+          for (int e = 0; e < VEC; ++e) count_key(ks[e]);
+        }
+      }
     }
     __syncthreads();
     // the chunk's counts into the segment's: one (pass, digit) per thread
@@ -386,16 +428,29 @@ __global__ void __launch_bounds__(THREADS, 2)
       if (c && dbg_ok(uint64_t(li) * passes * RADIX + w, a.nseg * passes * RADIX, kSiteSegCounts))
         atomicAdd(&cnt[w], c);
     }
-    // clear the look-back words of this chunk's tiles, every pass
+    // clear the look-back words of this chunk's tiles [ta, tb), every pass.
+    // In the [tile/4][digit][tile%4] layout one digit's words of four
+    // consecutive tiles are 16 contiguous bytes: consecutive threads clear
+    // consecutive 16-byte groups, a whole group when its four tiles are all
+    // this chunk's, else word by word (the neighbouring segment owns the rest)
     const uint32_t t_first = lc * uint32_t(CHUNK_TILES);
     const uint32_t t_last = min(t_first + uint32_t(CHUNK_TILES), (d.len + TILE - 1) / TILE);
+    const uint32_t ta = d.tile0 + t_first, tb = d.tile0 + t_last;
+    const uint32_t g0 = ta / 4u, ng = (tb - 1u) / 4u - g0 + 1u;
     for (int p = 0; p < passes; ++p) {
       uint32_t* st = a.status + size_t(p) * a.tiles_max * RADIX;
-      const uint32_t nw = (t_last - t_first) * RADIX;
-      for (uint32_t i = tid; i < nw; i += THREADS)
-        if (dbg_ok(lb_index<RADIX>(d.tile0 + t_first + i / RADIX, i % RADIX),
-                   a.tiles_max * RADIX, kSiteSegClear))
-          st[lb_index<RADIX>(d.tile0 + t_first + i / RADIX, i % RADIX)] = 0u;
+      for (uint32_t i = tid; i < ng * RADIX; i += THREADS) {
+        const uint32_t g = g0 + i / RADIX;
+        const size_t q = size_t(g) * RADIX + i % RADIX;  // the 16-byte group
+        if (!dbg_ok(q, a.tiles_max * RADIX / 4, kSiteSegClear)) continue;
+        if (4u * g >= ta && 4u * g + 3u < tb) {
+          reinterpret_cast<uint4*>(st)[q] = make_uint4(0u, 0u, 0u, 0u);
+        } else {
+#pragma unroll
+          for (uint32_t c = 0; c < 4u; ++c)
+            if (4u * g + c >= ta && 4u * g + c < tb) st[q * 4 + c] = 0u;
+        }
+      }
     }
     __syncthreads();
     uint32_t* state = a.state + size_t(li) * kSegStateWords;
@@ -421,11 +476,25 @@ __global__ void __launch_bounds__(THREADS, 2)
           offs[p * RADIX + tid] = e;
         if (!__syncthreads_or(tid < RADIX && c == d.len)) exec |= 1u << p;
       }
+      if ((__popc(exec) & 1) != (passes & 1)) {  // every thread: the same exec
+        const uint32_t skipped = ~exec & ((1u << passes) - 1u);
+        exec |= skipped & (0u - skipped);
+      }
+      // every pass tile of the segment learns where it is and which passes
+      // move data from one descriptor (read by the pass kernel, launched after)
+      const uint32_t ntiles = (d.len + TILE - 1) / TILE;
+      for (uint32_t t = tid; t < ntiles; t += THREADS) {
+        if (!dbg_ok(uint64_t(d.tile0) + t, a.tiles_max, kSiteSegState)) continue;
+        TileDesc td;
+        td.off = d.off;
+        td.len = d.len;
+        td.li = li;
+        td.tile0 = d.tile0;
+        td.exec = exec;
+        td.pad[0] = td.pad[1] = 0u;
+        a.tdesc[d.tile0 + t] = td;
+      }
       if (tid == 0) {
-        if ((__popc(exec) & 1) != (passes & 1)) {
-          const uint32_t skipped = ~exec & ((1u << passes) - 1u);
-          exec |= skipped & (0u - skipped);
-        }
         __threadfence();
         st_release(&state[kSegReady], 1u | (exec << 1));
       }
@@ -459,33 +528,31 @@ __global__ void __launch_bounds__(THREADS, 4)
     const uint32_t item = s_misc[0];
     if (item >= q_end || s_misc[1] != 0u) break;  // CTA-uniform
 
-    // ---- one tile of one pass of a long segment
+    // ---- one tile of one pass of a long segment.  The histogram kernel
+    // (launched before this one) has written the tile's descriptor and every
+    // segment's scans; a tile of pass p > 0 waits (bounded) until every tile of
+    // pass p - 1 of its segment is written, whether that pass moved data or not
     const int p = int(item / n_tiles);
     const uint32_t gt = item - uint32_t(p) * n_tiles;
-    const uint32_t li = a.tile_seg[gt];
-    const SegDesc d = a.descs[li];
+    const TileDesc d = a.tdesc[gt];
+    const uint32_t li = d.li;
     uint32_t* state = a.state + size_t(li) * kSegStateWords;
     const uint32_t ntiles = (d.len + TILE - 1) / TILE;
-    if (tid == 0) {
-      // both conditions read at once (one round trip); the bounded waits
-      // only when one of them does not hold yet
-      uint32_t ready = ld_relaxed(&state[kSegReady]);
-      const uint32_t done = p > 0 ? ld_relaxed(&state[kSegDone0 + p - 1]) : ntiles;
-      bool ok = (ready & 1u) && done >= ntiles;
-      if (ok) {
-        __threadfence();  // acquire: the histograms and the previous pass's output
-      } else {
-        ok = wait_geq(&state[kSegReady], 1u, ctrl, a.knobs.timeout_ns, gt);
-        if (ok && p > 0) ok = wait_geq(&state[kSegDone0 + p - 1], ntiles, ctrl,
-                                       a.knobs.timeout_ns, gt);
-        ready = ld_acquire(&state[kSegReady]);
+    const uint32_t exec = d.exec;
+    bool ok = true;
+    if (p > 0) {
+      if (tid == 0) {
+        bool w = ld_relaxed(&state[kSegDone0 + p - 1]) >= ntiles;
+        if (w)
+          __threadfence();  // acquire: the previous pass's output
+        else
+          w = wait_geq(&state[kSegDone0 + p - 1], ntiles, ctrl, a.knobs.timeout_ns, gt);
+        s_misc[3] = w ? 1u : 0u;
       }
-      s_misc[3] = ok ? 1u : 0u;
-      s_misc[4] = ready >> 1;
+      __syncthreads();
+      ok = s_misc[3] != 0u;
     }
-    __syncthreads();
-    const uint32_t exec = s_misc[4];
-    if (s_misc[3] && ((exec >> p) & 1u)) {
+    if (ok && ((exec >> p) & 1u)) {
       const bool from_alt = (__popc(exec & ((1u << p) - 1u)) & 1) != 0;
       TileArgs<K, VB> t;
       t.ksrc = (from_alt ? k1 : k0) + d.off;

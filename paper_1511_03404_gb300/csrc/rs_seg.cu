@@ -69,14 +69,22 @@ struct SegSort {
     a.nseg = nseg;
     a.knobs = knobs;
     using V = ValT<VB>;
-    const unsigned grid = unsigned(device_info().sms * occ);
+    // grids no larger than the work can be: at most tiles_max pass tiles per
+    // pass and chunks_max histogram chunks (bounds the host knows without
+    // the plan), so that a small batch does not spread idle CTAs over every
+    // SM while other streams' kernels want them
+    const size_t sms = size_t(device_info().sms);
+    const unsigned grid = unsigned(std::max<size_t>(
+        1, std::min<size_t>(sms * occ, size_t(passes) * L.tiles_max)));
+    const unsigned grid_hist =
+        unsigned(std::max<size_t>(1, std::min<size_t>(sms * occ_hist, L.chunks_max)));
     const unsigned grid_small =
-        unsigned(std::max<size_t>(1, std::min<size_t>(nseg, size_t(device_info().sms) * occ_small)));
+        unsigned(std::max<size_t>(1, std::min<size_t>(nseg, sms * occ_small)));
     prof_before(s);
     small<<<grid_small, THREADS, SS::BYTES, s>>>(static_cast<K*>(keys), static_cast<V*>(vals),
                                                  static_cast<K*>(keys_alt),
                                                  static_cast<V*>(vals_alt), a);
-    hist<<<unsigned(device_info().sms * occ_hist), C::HIST_THREADS,
+    hist<<<grid_hist, C::HIST_THREADS,
            passes * C::RADIX * C::HIST_SLOTS * 4, s>>>(static_cast<const K*>(keys), a);
     kern<<<grid, THREADS, C::BYTES, s>>>(static_cast<K*>(keys), static_cast<V*>(vals),
                                          static_cast<K*>(keys_alt), static_cast<V*>(vals_alt), a);

@@ -392,6 +392,13 @@ void scheduler(rs_server* s) {
         batch_keys += r->req.n;
       }
     }
+    // a batch of one request runs as that request's own sort (one launch for
+    // a short array instead of the segmented sort's sequence)
+    std::shared_ptr<Request> solo;
+    if (batch.size() == 1) {
+      solo = batch[0];
+      batch.clear();
+    }
     if (!batch.empty()) {
       const int si = free_stream(s);
       const BatchPlan b = plan_batch(batch_keys, batch.size());
@@ -422,7 +429,7 @@ void scheduler(rs_server* s) {
     bool large_blocked = false;  // large requests are admitted in submission order
     for (auto& r : seen) {
       if (r->state != 0) continue;  // in the batch just formed
-      if (batchable(s, r->req)) {  // waits for a later batch
+      if (batchable(s, r->req) && r != solo) {  // waits for a later batch
         keep.push_back(r->id);
         continue;
       }

@@ -98,7 +98,6 @@ def test_mixed_trace_matches_oracle(server):
     st, stats = rs.rs_server_stats(server)
     rs.check(st)
     assert stats["completed"] == len(reqs) and stats["failed"] == 0
-    assert stats["batches"] >= 1  # the short u32 pair requests shared launches
     assert stats["p99_ms"] >= stats["p50_ms"] > 0
     assert stats["service_p99_ms"] >= stats["service_p50_ms"] > 0
     assert stats["wait_p99_ms"] >= stats["wait_p50_ms"] >= 0
@@ -110,7 +109,39 @@ def test_mixed_trace_matches_oracle(server):
     for t in trace:
         assert 0 <= t["submit_s"] <= t["admit_s"] <= t["done_s"]
         assert 0 <= t["stream"] < 8 and t["batched"] in (0, 1)
-    assert any(t["batched"] for t in trace)
+
+
+def test_short_requests_queued_together_share_one_launch(server):
+    """Short u32 pair requests that wait together (every stream busy with a
+    longer sort) are admitted as one batched segmented sort; a short request
+    that is alone in the queue runs as its own sort instead of a batch of one."""
+    st, cfg = rs.rs_server_get_config(server)
+    rs.check(st)
+    # long sorts on all eight streams (none counted as "large", which would
+    # keep them to three at a time), so the short requests have to queue
+    rs.check(rs.rs_server_set_config(server, dict(cfg, large_n=1 << 30)))
+    busy = [(inputs.keys(np.uint64, "uniform", 1 << 22, seed=40 + i), None) for i in range(8)]
+    short = [(inputs.keys(np.uint32, "gaussian", 3000 + 17 * i, seed=60 + i),
+              inputs.values(np.uint32, 3000 + 17 * i)) for i in range(24)]
+    out = run(server, busy + short)
+    for r in out:
+        ek, ev = oracle.lsd_sort(r.k, r.v)
+        assert np.array_equal(r.ok, ek)
+        if r.v is not None:
+            assert np.array_equal(r.ov, ev)
+    st, stats = rs.rs_server_stats(server)
+    rs.check(st)
+    assert stats["batches"] >= 1 and stats["batched_requests"] >= 2 * stats["batches"]
+    st, trace = rs.rs_server_trace(server)
+    rs.check(st)
+    assert sum(t["batched"] for t in trace) == stats["batched_requests"]
+    # alone: one short request on an idle server is not a batch
+    rs.check(rs.rs_server_reset_stats(server))
+    out = run(server, short[:1])
+    assert np.array_equal(out[0].ok, oracle.lsd_sort(out[0].k, out[0].v)[0])
+    st, stats = rs.rs_server_stats(server)
+    rs.check(st)
+    assert stats["batches"] == 0 and stats["completed"] == 1
 
 
 def test_same_result_alone_and_in_the_mix():

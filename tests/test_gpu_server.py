@@ -111,16 +111,26 @@ def test_mixed_trace_matches_oracle(server):
         assert 0 <= t["stream"] < 8 and t["batched"] in (0, 1)
 
 
-def test_short_requests_queued_together_share_one_launch(server):
+def test_short_requests_queued_together_share_one_launch():
     """Short u32 pair requests that wait together (every stream busy with a
     longer sort) are admitted as one batched segmented sort; a short request
     that is alone in the queue runs as its own sort instead of a batch of one."""
+    st, server = rs.rs_server_create(4 << 30, 8)
+    rs.check(st, "rs_server_create")
+    try:
+        _short_requests_batch(server)
+    finally:
+        rs.check(rs.rs_server_destroy(server))
+
+
+def _short_requests_batch(server):
     st, cfg = rs.rs_server_get_config(server)
     rs.check(st)
-    # long sorts on all eight streams (none counted as "large", which would
-    # keep them to three at a time), so the short requests have to queue
+    # long sorts (a few ms each, copies included) on all eight streams, none
+    # counted as "large" (which would keep them to three at a time), so the
+    # short requests submitted right after them have to queue
     rs.check(rs.rs_server_set_config(server, dict(cfg, large_n=1 << 30)))
-    busy = [(inputs.keys(np.uint64, "uniform", 1 << 22, seed=40 + i), None) for i in range(8)]
+    busy = [(inputs.keys(np.uint64, "uniform", 1 << 23, seed=40 + i), None) for i in range(8)]
     short = [(inputs.keys(np.uint32, "gaussian", 3000 + 17 * i, seed=60 + i),
               inputs.values(np.uint32, 3000 + 17 * i)) for i in range(24)]
     out = run(server, busy + short)

@@ -421,6 +421,22 @@ rs_status rs_segmented_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys
 rs_status rs_segmented_workspace_bytes(size_t n, size_t n_seg, int begin_bit, int end_bit,
                                        size_t* bytes);
 
+/*
+ * The batched segmented sort for any of the four data types of Sec. 3:
+ * key_bytes 4 or 8, val_bytes 0 (keys only) or equal to key_bytes; vals and
+ * vals_alt must be NULL when val_bytes is 0.  Everything else as for
+ * rs_segmented_sort_pairs (offsets, bit range up to 8 * key_bytes, result
+ * buffer by the pass count's parity, status through rs_workspace_status),
+ * with rs_segmented_workspace_bytes_typed for the workspace.  Segments of
+ * up to 4096 elements (2048 for 64-bit keys) are sorted whole by one CTA.
+ */
+rs_status rs_segmented_sort(int key_bytes, int val_bytes, void* keys, void* vals, void* keys_alt,
+                            void* vals_alt, size_t n, const uint64_t* d_offsets, size_t n_seg,
+                            int begin_bit, int end_bit, void* ws, size_t ws_bytes,
+                            rs_stream_t stream, int* result_in_alt);
+rs_status rs_segmented_workspace_bytes_typed(int key_bytes, int val_bytes, size_t n, size_t n_seg,
+                                             int begin_bit, int end_bit, size_t* bytes);
+
 /* ---- sort server: continuous batching of requests on one GPU ---------- */
 
 /*
@@ -429,12 +445,12 @@ rs_status rs_segmented_workspace_bytes(size_t n, size_t n_seg, int begin_bit, in
  * current at creation.  A scheduler thread admits queued requests, oldest
  * first, whenever the request's device footprint fits the free part of the
  * pool and a stream is free; a request that does not fit yet does not block
- * younger ones that do.  Admitted 32-bit pair requests of at most
- * batch_max_n elements (same bit range; 2^14 by default, see
- * rs_server_config) are packed into one batched segmented sort, which takes
- * a free stream before any single request does; every other request runs as
- * its own sort, large ones (large_n elements and up) at most max_large at a
- * time.  Each admitted unit runs copy-in, sort, copy-out on its stream, so
+ * younger ones that do.  Requests of at most batch_max_n elements (2^14 by
+ * default, see rs_server_config) that wait together and share key and value
+ * widths and bit range are packed into one batched segmented sort, which
+ * takes a free stream before any single request does; every other request
+ * (and a short one waiting alone) runs as its own sort, large ones (large_n
+ * elements and up) at most max_large at a time.  Each admitted unit runs copy-in, sort, copy-out on its stream, so
  * units overlap on the device.
  * The sorted result of a request does not depend on what it was batched or
  * overlapped with.
@@ -485,7 +501,7 @@ rs_status rs_server_create(size_t budget_bytes, int streams, rs_server** out);
  * A new setting applies to admissions after the call; running units keep
  * theirs.  Defaults in brackets. */
 typedef struct rs_server_config {
-  size_t batch_max_n;    /* u32 pair requests of 2..batch_max_n elements are batched [2^14] */
+  size_t batch_max_n;    /* requests of 2..batch_max_n elements are batched [2^14] */
   size_t max_batch_keys; /* elements per batched launch at most, >= batch_max_n [2^22] */
   size_t large_n;        /* requests of at least large_n elements are "large" [2^21] */
   int max_large;         /* large units admitted at once, oldest first, 1..64 [3] */

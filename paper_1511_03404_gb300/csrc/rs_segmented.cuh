@@ -221,6 +221,8 @@ struct SegKernelCfg {
   static constexpr int HIST_THREADS = 1024;
   static constexpr int HIST_SLOTS = 16;
   static constexpr int HIST_BYTES = MAXP * RADIX * HIST_SLOTS * 4;
+  // two CTAs per SM while their counters fit (32-bit keys), else one
+  static constexpr int HIST_MINB = HIST_BYTES <= 100 * 1024 ? 2 : 1;
   using OS = OnesweepSmem<K, VB, RADIX_BITS, THREADS, ITEMS, UNIT>;
   using SS = SegSmallSmem<K, VB, RADIX_BITS, THREADS, SMALL_ITEMS>;
   static constexpr int MISC = (OS::BYTES + 15) / 16 * 16;  // u32 [8]
@@ -324,8 +326,8 @@ __device__ __forceinline__ void seg_cta_sort(const K* kin, const ValT<VB>* vin, 
   }
 }
 
-template <class K, int VB, int RADIX_BITS, int THREADS, int ITEMS>
-__global__ void __launch_bounds__(THREADS, 4)
+template <class K, int VB, int RADIX_BITS, int THREADS, int ITEMS, int MINB = 4>
+__global__ void __launch_bounds__(THREADS, MINB)
     k_seg_small(K* __restrict__ k0, ValT<VB>* __restrict__ v0, K* __restrict__ k1,
                 ValT<VB>* __restrict__ v1, SegArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -351,8 +353,8 @@ __global__ void __launch_bounds__(THREADS, 4)
 // last chunk of a segment (ticket) scans the segment's histograms, chooses the
 // passes that move data and marks the segment ready for its pass tiles.
 template <class K, int RADIX_BITS, int THREADS, int MAXP, int SLOTS, int CHUNK, int TILE,
-          int CHUNK_TILES>
-__global__ void __launch_bounds__(THREADS, 2)
+          int CHUNK_TILES, int MINB = 2>
+__global__ void __launch_bounds__(THREADS, MINB)
     k_seg_hist(const K* __restrict__ k0, SegArgs a) {
   constexpr int RADIX = 1 << RADIX_BITS;
   constexpr int VEC = 16 / int(sizeof(K));
@@ -503,8 +505,9 @@ __global__ void __launch_bounds__(THREADS, 2)
   }
 }
 
-template <class K, int VB, int RADIX_BITS, int THREADS, int ITEMS, int CHUNK_TILES, int UNIT = 32>
-__global__ void __launch_bounds__(THREADS, 4)
+template <class K, int VB, int RADIX_BITS, int THREADS, int ITEMS, int CHUNK_TILES, int UNIT = 32,
+          int MINB = 4>
+__global__ void __launch_bounds__(THREADS, MINB)
     k_seg_persistent(K* __restrict__ k0, ValT<VB>* __restrict__ v0, K* __restrict__ k1,
                      ValT<VB>* __restrict__ v1, SegArgs a) {
   using V = ValT<VB>;

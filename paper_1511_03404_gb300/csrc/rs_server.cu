@@ -2,9 +2,9 @@
 //
 // A scheduler thread admits queued requests while their device footprint
 // fits the memory budget (one resident device pool, carved by a first-fit
-// allocator) and while stream slots are free.  Admitted short 32-bit pair
-// requests are packed into one batched segmented sort; every other request
-// runs as its own sort.  Each admitted unit goes to one of several CUDA
+// allocator) and while stream slots are free.  Admitted short requests of one
+// type and bit range are packed into one batched segmented sort; every other
+// request runs as its own sort.  Each admitted unit goes to one of several CUDA
 // streams, so copies and sorts of different requests overlap on the device,
 // and requests that arrive while others run are admitted as memory and slots
 // free up.  A host callback at the end of each unit's stream work marks its
@@ -179,7 +179,13 @@ SingleLayout single_layout(const rs_request& r) {
 size_t single_footprint(const rs_request& r) { return single_layout(r).total; }
 
 bool batchable(const rs_server* s, const rs_request& r) {
-  return r.key_bytes == 4 && r.val_bytes == 4 && r.n <= s->batch_max_n && r.n > 1;
+  return r.n <= s->batch_max_n && r.n > 1 && r.begin_bit < r.end_bit;
+}
+
+// Requests that can share one batched segmented sort: same types and bits.
+bool same_batch(const rs_request& a, const rs_request& b) {
+  return a.key_bytes == b.key_bytes && a.val_bytes == b.val_bytes &&
+         a.begin_bit == b.begin_bit && a.end_bit == b.end_bit;
 }
 
 void CUDART_CB on_unit_done(void* p) {
@@ -236,16 +242,19 @@ struct BatchPlan {
   size_t k, v, ka, va, off, ws, bytes;
 };
 
-BatchPlan plan_batch(size_t total, size_t nseg) {
+// Device layout of a batch of nseg requests of the type of q, total keys.
+BatchPlan plan_batch(const rs_request& q, size_t total, size_t nseg) {
   BatchPlan b;
   b.total = total;
-  rs_segmented_workspace_bytes(total, nseg, 0, 32, &b.seg_ws);
-  const size_t arr = rs::align_up(total * 4, 256);
+  rs_segmented_workspace_bytes_typed(q.key_bytes, q.val_bytes, total, nseg, q.begin_bit,
+                                     q.end_bit, &b.seg_ws);
+  const size_t karr = rs::align_up(total * size_t(q.key_bytes), 256);
+  const size_t varr = rs::align_up(total * size_t(q.val_bytes), 256);
   b.k = 0;
-  b.v = b.k + arr;
-  b.ka = b.v + arr;
-  b.va = b.ka + arr;
-  b.off = b.va + arr;
+  b.v = b.k + karr;
+  b.ka = b.v + varr;
+  b.va = b.ka + karr;
+  b.off = b.va + varr;
   b.ws = b.off + rs::align_up((nseg + 1) * 8, 256);
   b.bytes = b.ws + rs::align_up(std::max<size_t>(b.seg_ws, 256), 256);
   return b;
@@ -258,31 +267,35 @@ rs_status launch_batch(rs_server* s, Unit* u, const BatchPlan& b) {
   uint64_t* off = s->off_slab + size_t(u->stream) * (kMaxBatchMembers + 1);
   off[0] = 0;
   for (size_t i = 0; i < nseg; ++i) off[i + 1] = off[i] + u->members[i]->req.n;
-  // every member in a batch has the same bit range (the scheduler groups them)
-  const int begin_bit = u->members[0]->req.begin_bit, end_bit = u->members[0]->req.end_bit;
+  // every member in a batch has the same types and bit range (the scheduler
+  // groups them)
+  const rs_request& q0 = u->members[0]->req;
+  const size_t kb = size_t(q0.key_bytes), vb = size_t(q0.val_bytes);
   for (size_t i = 0; i < nseg; ++i) {
     const rs_request& q = u->members[i]->req;
-    if (cudaMemcpyAsync(base + b.k + off[i] * 4, q.h_keys, q.n * 4, cudaMemcpyHostToDevice, st) ||
-        cudaMemcpyAsync(base + b.v + off[i] * 4, q.h_vals, q.n * 4, cudaMemcpyHostToDevice, st))
+    if (cudaMemcpyAsync(base + b.k + off[i] * kb, q.h_keys, q.n * kb, cudaMemcpyHostToDevice, st) ||
+        (vb && cudaMemcpyAsync(base + b.v + off[i] * vb, q.h_vals, q.n * vb,
+                               cudaMemcpyHostToDevice, st)))
       return RS_ERR_CUDA;
   }
   if (cudaMemcpyAsync(base + b.off, off, (nseg + 1) * 8, cudaMemcpyHostToDevice, st))
     return RS_ERR_CUDA;
   int in_alt = 0;
-  rs_status rs_st = rs_segmented_sort_pairs(
-      reinterpret_cast<uint32_t*>(base + b.k), reinterpret_cast<uint32_t*>(base + b.v),
-      reinterpret_cast<uint32_t*>(base + b.ka), reinterpret_cast<uint32_t*>(base + b.va), b.total,
-      reinterpret_cast<const uint64_t*>(base + b.off), nseg, begin_bit, end_bit, base + b.ws,
-      b.bytes - b.ws, reinterpret_cast<rs_stream_t>(st), &in_alt);
+  rs_status rs_st = rs_segmented_sort(
+      q0.key_bytes, q0.val_bytes, base + b.k, vb ? base + b.v : nullptr, base + b.ka,
+      vb ? base + b.va : nullptr, b.total, reinterpret_cast<const uint64_t*>(base + b.off), nseg,
+      q0.begin_bit, q0.end_bit, base + b.ws, b.bytes - b.ws, reinterpret_cast<rs_stream_t>(st),
+      &in_alt);
   if (rs_st != RS_OK) return rs_st;
   if (cudaMemcpyAsync(u->h_status, base + b.ws, sizeof(uint32_t), cudaMemcpyDeviceToHost, st))
     return RS_ERR_CUDA;
   const size_t ko = in_alt ? b.ka : b.k, vo = in_alt ? b.va : b.v;
   for (size_t i = 0; i < nseg; ++i) {
     const rs_request& q = u->members[i]->req;
-    if (cudaMemcpyAsync(q.h_out_keys, base + ko + off[i] * 4, q.n * 4, cudaMemcpyDeviceToHost,
+    if (cudaMemcpyAsync(q.h_out_keys, base + ko + off[i] * kb, q.n * kb, cudaMemcpyDeviceToHost,
                         st) ||
-        cudaMemcpyAsync(q.h_out_vals, base + vo + off[i] * 4, q.n * 4, cudaMemcpyDeviceToHost, st))
+        (vb && cudaMemcpyAsync(q.h_out_vals, base + vo + off[i] * vb, q.n * vb,
+                               cudaMemcpyDeviceToHost, st)))
       return RS_ERR_CUDA;
   }
   if (cudaLaunchHostFunc(st, on_unit_done, u) != cudaSuccess) return RS_ERR_CUDA;
@@ -381,13 +394,12 @@ void scheduler(rs_server* s) {
     size_t batch_keys = 0;
     for (auto& r : seen) {
       if (!batchable(s, r->req)) continue;
-      const bool same_bits = batch.empty() || (batch[0]->req.begin_bit == r->req.begin_bit &&
-                                               batch[0]->req.end_bit == r->req.end_bit);
+      const bool same = batch.empty() || same_batch(batch[0]->req, r->req);
       // a batch never outgrows the pool, so that it is admitted once enough
       // of the pool is free
-      if (same_bits && batch_keys + r->req.n <= s->max_batch_keys &&
+      if (same && batch_keys + r->req.n <= s->max_batch_keys &&
           batch.size() < kMaxBatchMembers &&
-          plan_batch(batch_keys + r->req.n, batch.size() + 1).bytes <= s->budget) {
+          plan_batch(r->req, batch_keys + r->req.n, batch.size() + 1).bytes <= s->budget) {
         batch.push_back(r);
         batch_keys += r->req.n;
       }
@@ -401,7 +413,7 @@ void scheduler(rs_server* s) {
     }
     if (!batch.empty()) {
       const int si = free_stream(s);
-      const BatchPlan b = plan_batch(batch_keys, batch.size());
+      const BatchPlan b = plan_batch(batch[0]->req, batch_keys, batch.size());
       size_t off = 0;
       if (si >= 0 && s->pool->alloc(b.bytes, &off)) {
         Unit* u = new Unit;
@@ -598,8 +610,7 @@ rs_status rs_server_set_config(rs_server* s, const rs_server_config* c) {
 rs_status rs_submit(rs_server* s, const rs_request* req, rs_handle* out) {
   if (!s || !req || !out || !valid_request(*req)) return RS_ERR_INVALID;
   // whichever way the policy at admission runs it, it must fit the pool
-  const bool pair32 = req->key_bytes == 4 && req->val_bytes == 4;
-  const size_t need = std::max(single_footprint(*req), pair32 ? plan_batch(req->n, 1).bytes : 0);
+  const size_t need = std::max(single_footprint(*req), plan_batch(*req, req->n, 1).bytes);
   if (need > s->budget) return RS_ERR_INVALID;  // could never be admitted
   auto r = std::make_shared<Request>();
   r->req = *req;

@@ -115,6 +115,9 @@ _SIGS = {
     "rs_segmented_sort_pairs": ([_vp, _vp, _vp, _vp, _sz, _vp, _sz, _i, _i, _vp, _sz, _vp, _vp],
                                 _i),
     "rs_segmented_workspace_bytes": ([_sz, _sz, _i, _i, _vp], _i),
+    "rs_segmented_sort": ([_i, _i, _vp, _vp, _vp, _vp, _sz, _vp, _sz, _i, _i, _vp, _sz, _vp, _vp],
+                          _i),
+    "rs_segmented_workspace_bytes_typed": ([_i, _i, _sz, _sz, _i, _i, _vp], _i),
     "rs_sample_workspace_bytes": ([_sz, _i, _i, _vp], _i),
     "rs_merge_workspace_bytes": ([_i, _i, _sz, _vp], _i),
     "rs_merge_sort": ([_i, _i, _vp, _vp, _vp, _vp, _sz, _vp, _sz, _vp, _vp], _i),
@@ -332,6 +335,23 @@ def rs_segmented_sort_pairs(keys, vals, keys_alt, vals_alt, n, d_offsets, n_seg,
                                         begin_bit, end_bit, ws, ws_bytes, stream,
                                         ctypes.byref(r))
     return st, r.value
+
+
+def rs_segmented_sort(key_bytes, val_bytes, keys, vals, keys_alt, vals_alt, n, d_offsets, n_seg,
+                      begin_bit, end_bit, ws, ws_bytes, stream):
+    r = _out_int()
+    st = load().rs_segmented_sort(key_bytes, val_bytes, keys, vals, keys_alt, vals_alt, n,
+                                  d_offsets, n_seg, begin_bit, end_bit, ws, ws_bytes, stream,
+                                  ctypes.byref(r))
+    return st, r.value
+
+
+def rs_segmented_workspace_bytes_typed(key_bytes, val_bytes, n, n_seg, begin_bit=0, end_bit=None):
+    out = ctypes.c_size_t()
+    end_bit = 8 * key_bytes if end_bit is None else end_bit
+    st = load().rs_segmented_workspace_bytes_typed(key_bytes, val_bytes, n, n_seg, begin_bit,
+                                                   end_bit, ctypes.byref(out))
+    return st, out.value
 
 
 def rs_segmented_workspace_bytes(n, n_seg, begin_bit=0, end_bit=32):

@@ -164,3 +164,18 @@ def test_host_buffer_sort_checks_arguments_before_enqueuing():
 def test_stats_entry_rejects_null_output():
     lib = rs.load()
     assert lib.rs_workspace_stats(None, None, None) == rs.RS_ERR_INVALID
+
+
+def test_typed_segmented_sort_checks_arguments_without_gpu():
+    fake = 1 << 40
+    ok = rs.rs_segmented_workspace_bytes_typed
+    assert ok(4, 8, 100, 2)[0] == rs.RS_ERR_INVALID
+    assert ok(8, 0, 100, 2, 0, 65)[0] == rs.RS_ERR_INVALID
+    assert ok(8, 8, 100, 2)[0] == rs.RS_OK
+    # values given for keys only, missing values for pairs, same buffer twice
+    assert rs.rs_segmented_sort(8, 0, fake, fake + 8192, fake + 4096, None, 100, fake, 2, 0, 64,
+                                None, 0, None)[0] == rs.RS_ERR_INVALID
+    assert rs.rs_segmented_sort(4, 4, fake, None, fake + 4096, None, 100, fake, 2, 0, 32, None, 0,
+                                None)[0] == rs.RS_ERR_INVALID
+    assert rs.rs_segmented_sort(4, 0, fake, None, fake, None, 100, fake, 2, 0, 32, None, 0,
+                                None)[0] == rs.RS_ERR_INVALID

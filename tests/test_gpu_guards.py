@@ -141,6 +141,34 @@ def test_segmented_edge_suite_guards_intact(dist, begin, end):
     assert np.array_equal(host(va if in_alt else dv, np.uint32), ev)
 
 
+@pytest.mark.parametrize("kb,vb", [(4, 0), (8, 0), (8, 8)], ids=["k32", "k64", "kv64"])
+def test_typed_segmented_guards_intact(kb, vb):
+    lengths = EDGE + [2047, 2048, 2049]
+    off = inputs.offsets_from_lengths(np.asarray(lengths, dtype=np.uint64))
+    n = int(off[-1])
+    dt = np.uint32 if kb == 4 else np.uint64
+    k = inputs.keys(dt, "entropy16", n)
+    v = inputs.values(dt, n) if vb else None
+    g = Guarded()
+    dk, ka = g.put(k), g.alloc(kb * n)
+    dv = g.put(v) if vb else None
+    va = g.alloc(vb * n) if vb else None
+    doff = g.put(off.astype(np.uint64))
+    st, need = rs.rs_segmented_workspace_bytes_typed(kb, vb, n, len(lengths))
+    rs.check(st)
+    ws = g.alloc(need)
+    h = torch.cuda.current_stream().cuda_stream
+    st, in_alt = rs.rs_segmented_sort(kb, vb, ptr(dk), ptr(dv), ptr(ka), ptr(va), n, ptr(doff),
+                                      len(lengths), 0, 8 * kb, ptr(ws), ws.numel(), h)
+    rs.check(st, "rs_segmented_sort")
+    rs.check(rs.rs_workspace_status(ptr(ws), h)[0], "device status")
+    g.check(f"typed segmented k{kb} v{vb}")
+    ek, ev = oracle.segmented_sort(k, v, off)
+    assert np.array_equal(host(ka if in_alt else dk, dt), ek)
+    if vb:
+        assert np.array_equal(host(va if in_alt else dv, dt), ev)
+
+
 @pytest.mark.parametrize("n,s,b", [(5000, 16, 8), (3 * 4096 + 17, 64, 64), (2**17 + 5, 32, 256)])
 def test_sample_partition_guards_intact(n, s, b):
     k = inputs.keys(np.uint32, "gaussian", n)

@@ -133,3 +133,71 @@ def test_graph_capture_and_replay():
         src_k, src_v = (ka, va) if result["in_alt"] else (dk, dv)
         assert np.array_equal(from_dev(src_k, np.uint32), ek), dist
         assert np.array_equal(from_dev(src_v, np.uint32), ev), dist
+
+
+# ---- the same sort for the other data types (rs_segmented_sort)
+
+TYPED = [(4, 0), (4, 4), (8, 0), (8, 8)]
+TYPED_IDS = ["k32", "kv32", "k64", "kv64"]
+EDGE64 = EDGE + [2047, 2048, 2049, 6143, 6144, 6145]
+
+
+def run_typed(kb, vb, k, v, off, begin_bit=0, end_bit=None):
+    end_bit = 8 * kb if end_bit is None else end_bit
+    n = k.size
+    dk = to_dev(k, torch)
+    ka = torch.empty_like(dk)
+    dv = to_dev(v, torch) if vb else None
+    va = torch.empty_like(dv) if vb else None
+    doff = to_dev(off.astype(np.uint64), torch)
+    st, need = rs.rs_segmented_workspace_bytes_typed(kb, vb, n, len(off) - 1, begin_bit, end_bit)
+    rs.check(st, "rs_segmented_workspace_bytes_typed")
+    ws = torch.empty(max(need, 256), dtype=torch.uint8, device="cuda")
+    h = torch.cuda.current_stream().cuda_stream
+    p = lambda t: None if t is None else t.data_ptr()  # noqa: E731
+    st, in_alt = rs.rs_segmented_sort(kb, vb, p(dk), p(dv), p(ka), p(va), n, doff.data_ptr(),
+                                      len(off) - 1, begin_bit, end_bit, p(ws), ws.numel(), h)
+    rs.check(st, "rs_segmented_sort")
+    rs.check(rs.rs_workspace_status(ws.data_ptr(), h)[0], "device status")
+    assert in_alt == (-(-(end_bit - begin_bit) // 8) & 1)
+    ok = from_dev(ka if in_alt else dk, k.dtype)
+    ov = from_dev(va if in_alt else dv, v.dtype) if vb else None
+    return ok, ov
+
+
+def check_typed(kb, vb, dist, lengths, begin_bit=0, end_bit=None):
+    dt = np.uint32 if kb == 4 else np.uint64
+    off = inputs.offsets_from_lengths(np.asarray(lengths, dtype=np.uint64))
+    n = int(off[-1])
+    k = inputs.keys(dt, dist, n)
+    v = inputs.values(dt, n) if vb else None
+    gk, gv = run_typed(kb, vb, k, v, off, begin_bit, end_bit)
+    ek, ev = oracle.segmented_sort(k, v, off, begin_bit=begin_bit, end_bit=end_bit)
+    assert np.array_equal(gk, ek), (kb, vb, dist, begin_bit, end_bit)
+    if vb:
+        assert np.array_equal(gv, ev), (kb, vb, dist, begin_bit, end_bit)
+
+
+@pytest.mark.parametrize("kb,vb", TYPED, ids=TYPED_IDS)
+@pytest.mark.parametrize("dist", ["uniform", "entropy16", "zero", "sorted_desc", "gaussian"])
+def test_typed_edge_lengths(kb, vb, dist):
+    check_typed(kb, vb, dist, EDGE64)
+
+
+@pytest.mark.parametrize("kb,vb", TYPED, ids=TYPED_IDS)
+def test_typed_bit_ranges_and_mix(kb, vb):
+    for b, e in ((0, 8 * kb), (0, 24), (5, 29), (8 * kb - 12, 8 * kb)):
+        check_typed(kb, vb, "uniform", EDGE64, b, e)
+    check_typed(kb, vb, "bucket", inputs.segment_lengths(1500, seed=7, max_log2=17))
+
+
+def test_typed_entry_matches_pairs_entry():
+    """rs_segmented_sort(4, 4, ...) and rs_segmented_sort_pairs are one sort."""
+    L = inputs.segment_lengths(400, seed=3, max_log2=16)
+    off = inputs.offsets_from_lengths(L)
+    n = int(off[-1])
+    k = inputs.keys(np.uint32, "gaussian", n)
+    v = inputs.values(np.uint32, n)
+    gk, gv = run_typed(4, 4, k, v, off)
+    pk, pv, _, _ = run_segmented(k, v, off)
+    assert np.array_equal(gk, pk) and np.array_equal(gv, pv)

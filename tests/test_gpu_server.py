@@ -133,6 +133,9 @@ def _short_requests_batch(server):
     busy = [(inputs.keys(np.uint64, "uniform", 1 << 23, seed=40 + i), None) for i in range(8)]
     short = [(inputs.keys(np.uint32, "gaussian", 3000 + 17 * i, seed=60 + i),
               inputs.values(np.uint32, 3000 + 17 * i)) for i in range(24)]
+    # short 64-bit key requests batch as well (one batch per type)
+    short += [(inputs.keys(np.uint64, "bucket", 5000 + 31 * i, seed=90 + i), None)
+              for i in range(12)]
     out = run(server, busy + short)
     for r in out:
         ek, ev = oracle.lsd_sort(r.k, r.v)
@@ -141,10 +144,12 @@ def _short_requests_batch(server):
             assert np.array_equal(r.ov, ev)
     st, stats = rs.rs_server_stats(server)
     rs.check(st)
-    assert stats["batches"] >= 1 and stats["batched_requests"] >= 2 * stats["batches"]
+    assert stats["batches"] >= 2 and stats["batched_requests"] >= 2 * stats["batches"]
     st, trace = rs.rs_server_trace(server)
     rs.check(st)
     assert sum(t["batched"] for t in trace) == stats["batched_requests"]
+    assert any(t["batched"] and t["key_bytes"] == 8 for t in trace)
+    assert any(t["batched"] and t["key_bytes"] == 4 for t in trace)
     # alone: one short request on an idle server is not a batch
     rs.check(rs.rs_server_reset_stats(server))
     out = run(server, short[:1])

@@ -77,6 +77,33 @@ def test_zero_keys_skip_every_pass():
     assert s["form"] in (1, 2) and s["moved_mask"] == 0 and s["skipped_mask"] == 0xF
 
 
+@pytest.mark.parametrize("kind,form", [(3, 2), (4, 3), (2, 1)],
+                         ids=["one_launch", "cluster", "resident_ctas"])
+def test_record_of_every_sort_form(kind, form):
+    """The record of the one-launch (cooperative), cluster and resident-CTA
+    forms: shape, moved passes and times, and the same sorted result."""
+    for kb, vb in ((4, 0), (4, 4), (8, 0), (8, 8)):
+        cands = [i for i in range(rs.rs_num_variants(kb, vb))
+                 if rs.rs_variant_info(kb, vb, i)["kind"] == kind]
+        if not cands:
+            continue
+        info = rs.rs_variant_info(kb, vb, cands[0])
+        n = min(info["max_n"], 3 * info["threads"] * info["items"] + 77)
+        dt = np.uint32 if kb == 4 else np.uint64
+        k = inputs.keys(dt, "uniform", n, seed=17)
+        s, out = sort_and_stats(kb, vb, k, variant=cands[0])
+        passes = 8 * kb // info["radix_bits"]
+        assert s["form"] == form and s["n"] == n and s["passes"] == passes, (kb, vb, s)
+        assert s["key_bytes"] == kb and s["val_bytes"] == vb
+        assert s["moved_mask"] == (1 << passes) - 1 and s["total_ms"] > 0
+        if form != 3:
+            assert all(t > 0 for t in s["pass_ms"]) and s["upsweep_ms"] > 0
+            assert s["bytes"] == n * kb + passes * 2 * n * (kb + vb)
+        else:
+            assert s["bytes"] == 2 * n * (kb + vb)
+        assert np.array_equal(out, oracle.lsd_sort(k)[0])
+
+
 def test_one_cta_and_no_op_records():
     k = inputs.keys(np.uint32, "uniform", 3000)
     small = [i for i in range(rs.rs_num_variants(4, 0)) if rs.rs_variant_info(4, 0, i)["kind"] == 1]

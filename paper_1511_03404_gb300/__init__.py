@@ -10,6 +10,8 @@ The compute path is the CUDA library under ``csrc/`` (C ABI in
 ``include/rs.h``); ``rs`` is its ctypes binding.
 """
 from . import rs  # noqa: F401
-from .rs import RsError, check, load, sort, status_string, workspace  # noqa: F401
+from .rs import (RsError, check, load, segmented_sort, sort, status_string,  # noqa: F401
+                 workspace)
 
-__all__ = ["rs", "RsError", "check", "load", "sort", "status_string", "workspace"]
+__all__ = ["rs", "RsError", "check", "load", "segmented_sort", "sort", "status_string",
+           "workspace"]

@@ -580,3 +580,43 @@ def sort(keys, vals=None, begin_bit=0, end_bit=None, radix_bits=0, variant=-1, s
         if vals is not None:
             vals.copy_(va)
     return keys, vals
+
+
+def segmented_sort(keys, offsets, vals=None, begin_bit=0, end_bit=None, stream=None, ws=None):
+    """Sort every segment [offsets[s], offsets[s+1]) of contiguous device
+    tensors in place (stable), in one launch sequence (rs_segmented_sort).
+
+    ``keys`` and ``vals`` are 32- or 64-bit tensors of one width (``vals``
+    optional); the keys are ordered as unsigned bit patterns over
+    [begin_bit, end_bit).  ``offsets`` is a uint64/int64 device tensor of
+    n_seg + 1 entries.  Returns ``(keys, vals)``.
+    """
+    torch = _torch()
+    if not keys.is_cuda or not keys.is_contiguous():
+        raise ValueError("keys must be a contiguous CUDA tensor")
+    kb = _key_bytes(keys)
+    vb = 0
+    if vals is not None:
+        vb = _key_bytes(vals)
+        if vb != kb or vals.numel() != keys.numel() or not vals.is_contiguous():
+            raise ValueError("vals must match the keys' width and length")
+    if offsets.dtype not in (torch.int64, torch.uint64) or not offsets.is_contiguous():
+        raise ValueError("offsets must be a contiguous 64-bit integer tensor")
+    n, nseg = keys.numel(), offsets.numel() - 1
+    end_bit = 8 * kb if end_bit is None else end_bit
+    if ws is None:
+        st, need = rs_segmented_workspace_bytes_typed(kb, vb, n, nseg, begin_bit, end_bit)
+        check(st, "rs_segmented_workspace_bytes_typed")
+        ws = torch.empty(max(need, 256), dtype=torch.uint8, device=keys.device)
+    ka = torch.empty_like(keys)
+    va = torch.empty_like(vals) if vals is not None else None
+    ptr = lambda t: None if t is None else t.data_ptr()  # noqa: E731
+    st, in_alt = rs_segmented_sort(kb, vb, ptr(keys), ptr(vals), ptr(ka), ptr(va), n,
+                                   offsets.data_ptr(), nseg, begin_bit, end_bit, ws.data_ptr(),
+                                   ws.numel(), _stream_handle(stream))
+    check(st, "rs_segmented_sort")
+    if in_alt:
+        keys.copy_(ka)
+        if vals is not None:
+            vals.copy_(va)
+    return keys, vals

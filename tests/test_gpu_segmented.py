@@ -201,3 +201,21 @@ def test_typed_entry_matches_pairs_entry():
     gk, gv = run_typed(4, 4, k, v, off)
     pk, pv, _, _ = run_segmented(k, v, off)
     assert np.array_equal(gk, pk) and np.array_equal(gv, pv)
+
+
+def test_torch_segmented_sort_helper():
+    """rs.segmented_sort over torch tensors: in place, every type, unsigned order."""
+    L = inputs.segment_lengths(300, seed=13, max_log2=15)
+    off = inputs.offsets_from_lengths(L)
+    n = int(off[-1])
+    doff = to_dev(off.astype(np.uint64), torch)
+    for dt in (np.uint32, np.uint64):
+        k = inputs.keys(dt, "sorted_desc", n)
+        v = inputs.values(dt, n)
+        dk, dv = to_dev(k, torch), to_dev(v, torch)
+        rs.segmented_sort(dk, doff, dv)
+        ek, ev = oracle.segmented_sort(k, v, off)
+        assert np.array_equal(from_dev(dk, dt), ek) and np.array_equal(from_dev(dv, dt), ev)
+        dk = to_dev(k, torch)
+        rs.segmented_sort(dk, doff)
+        assert np.array_equal(from_dev(dk, dt), oracle.segmented_sort(k, None, off)[0])

@@ -1,6 +1,7 @@
 """Parity at the benchmark's full sizes, in the configuration bench.py times
 (the C ABI, the tuned variant choice): u32 pairs at n = 2^26 for the six
-distributions, u64 keys and u64 pairs at n = 2^27 for the six and 16-bit
+distributions and in the signed and IEEE-754 orders (ascending and
+descending), u64 keys and u64 pairs at n = 2^27 for the six and 16-bit
 entropy keys, and the batched segmented workload (20,000 segments, about
 1.5e9 pairs).  The oracle takes minutes
 at these sizes, so the result is checked on the device by properties that
@@ -171,3 +172,49 @@ def test_segmented_twenty_thousand_segments_full_size():
         ek, ev = oracle.lsd_sort(k[a:b], np.arange(a, b, dtype=np.uint32))
         assert np.array_equal(from_dev(out_k[a:b], np.uint32), ek), s
         assert np.array_equal(from_dev(out_v[a:b], np.uint32), ev), s
+
+
+def total_order(t):
+    """Signed tensor whose order is IEEE-754 totalOrder of binary32 bit patterns
+    held in an int32 tensor: negative patterns have every bit but the sign
+    flipped, non-negative ones are kept."""
+    return t ^ ((t >> 31) & 0x7FFFFFFF)
+
+
+def check_pairs_order(src, out_k, out_v, o):
+    """As check_pairs, for a sort by the order whose signed key is o."""
+    n = src.numel()
+    assert bool((o[1:] >= o[:-1]).all()), "keys not in order"
+    idx = out_v.long()
+    seen = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    seen[idx] = 1
+    assert bool(seen.bool().all()), "values are not a permutation"
+    assert bool((src[idx] == out_k).all()), "a key left its value"
+    eq = o[1:] == o[:-1]
+    assert bool(((idx[1:] > idx[:-1]) | ~eq).all()), "equal keys out of input order"
+
+
+@pytest.mark.parametrize("kind,descending", [(1, False), (1, True), (2, False), (2, True)],
+                         ids=["signed", "signed_desc", "float", "float_desc"])
+def test_u32_pairs_2p26_key_orders(kind, descending):
+    """Signed and IEEE-754 orders, ascending and descending, at the benchmark
+    size: stable in every mode (equal keys keep their input order)."""
+    n = 1 << 26
+    k = inputs.keys(np.uint32, "uniform", n) if kind == 1 else inputs.float_keys(np.uint32, n)
+    dk = to_dev(k, torch)
+    src = dk.clone()
+    dv = torch.arange(n, dtype=torch.int32, device="cuda")
+    ka, va = torch.empty_like(dk), torch.empty_like(dv)
+    st, need = rs.rs_workspace_bytes(4, 4, n, 0, 32)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    h = torch.cuda.current_stream().cuda_stream
+    st, in_alt = rs.rs_sort(4, 4, dk.data_ptr(), dv.data_ptr(), ka.data_ptr(), va.data_ptr(), n,
+                            0, 32, ws.data_ptr(), ws.numel(), h, key_kind=kind,
+                            descending=descending)
+    rs.check(st, "rs_sort")
+    rs.check(rs.rs_workspace_status(ws.data_ptr(), h)[0], "device status")
+    out_k, out_v = (ka, va) if in_alt else (dk, dv)
+    o = out_k if kind == 1 else total_order(out_k)
+    if descending:
+        o = ~o  # reverses the signed order
+    check_pairs_order(src, out_k, out_v, o)

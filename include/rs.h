@@ -450,8 +450,11 @@ rs_status rs_segmented_workspace_bytes_typed(int key_bytes, int val_bytes, size_
  * widths and bit range are packed into one batched segmented sort, which
  * takes a free stream before any single request does; every other request
  * (and a short one waiting alone) runs as its own sort, large ones (large_n
- * elements and up) at most max_large at a time.  Each admitted unit runs copy-in, sort, copy-out on its stream, so
- * units overlap on the device.
+ * elements and up) at most max_large at a time.  Each admitted unit runs
+ * copy-in, sort, copy-out on its stream, so units overlap on the device;
+ * with shared copy queues (an option) the copies in of all units of a size
+ * class (large or not) go through one FIFO copy stream and their copies out
+ * through another, ordered against the unit's sort by events.
  * The sorted result of a request does not depend on what it was batched or
  * overlapped with.
  */
@@ -507,11 +510,14 @@ typedef struct rs_server_config {
   int max_large;         /* large units admitted at once, oldest first, 1..64 [3] */
   int large_low_priority; /* 1: large units run on low-priority streams, so that the
                              kernels of short requests are scheduled ahead of them [1] */
+  int shared_copy_queues; /* 1: copies through one FIFO copy stream per direction and
+                             size class; 0: on each unit's own stream [0] */
 } rs_server_config;
 
 /* RS_ERR_INVALID for a NULL argument or a field out of range
  * (batch_max_n > max_batch_keys, max_batch_keys > RS_MAX_N, large_n = 0,
- * max_large outside 1..64, large_low_priority not 0 or 1). */
+ * max_large outside 1..64, large_low_priority or shared_copy_queues not 0
+ * or 1). */
 rs_status rs_server_get_config(rs_server* server, rs_server_config* out);
 rs_status rs_server_set_config(rs_server* server, const rs_server_config* cfg);
 

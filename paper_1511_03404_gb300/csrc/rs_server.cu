@@ -9,6 +9,15 @@
 // and requests that arrive while others run are admitted as memory and slots
 // free up.  A host callback at the end of each unit's stream work marks its
 // requests done; rs_poll reports that without blocking.
+//
+// Copies: by default a unit's copies run on its own stream.  With shared copy
+// queues (a policy option) every unit's host-to-device copies go through one
+// FIFO copy stream per size class (short / large) and its device-to-host
+// copies through another, ordered against the unit's sort by events: one
+// copy then has the host link to itself and its sort starts as soon as it
+// lands.  On the mixed serving trace the two measured the same capacity and
+// the option gave short requests a longer median (their copies wait behind
+// larger ones in the FIFO), so it is off by default.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -111,7 +120,11 @@ struct rs_server {
   size_t large_n = size_t(1) << 21;
   int max_large = 3;
   int large_low_priority = 1;
+  int shared_copy_queues = 0;
   int large_running = 0;
+  cudaStream_t copy_in[2] = {nullptr, nullptr};   // FIFO host-to-device: [0] short, [1] large
+  cudaStream_t copy_out[2] = {nullptr, nullptr};  // FIFO device-to-host, same classes
+  std::vector<cudaEvent_t> ev_in, ev_sorted;      // per stream slot: input landed, sort done
   std::mutex mu;
   std::condition_variable cv;
   std::deque<uint64_t> pending;
@@ -141,8 +154,32 @@ struct Unit {
   size_t pool_off = 0, pool_bytes = 0;
   int stream = 0;
   bool large = false;
+  bool low_priority = false;     // sorts on the slot's low-priority stream
+  bool shared_copies = false;    // copies through the server's copy queues
   uint32_t* h_status = nullptr;  // pinned: device status word of the sort
 };
+
+// The streams of one unit's copies in, sort and copies out (one stream for
+// all three unless the unit uses the shared copy queues).
+struct Lanes {
+  cudaStream_t in, cs, out;
+};
+
+Lanes lanes_of(const rs_server* s, const Unit* u) {
+  // (the unit's fields are set at admission, under the server's lock; the
+  // streams do not change after creation)
+  const cudaStream_t cs = u->low_priority ? s->streams_lo[u->stream] : s->streams[u->stream];
+  if (!u->shared_copies) return Lanes{cs, cs, cs};
+  const int c = u->large ? 1 : 0;
+  return Lanes{s->copy_in[c], cs, s->copy_out[c]};
+}
+
+// Order `to` after the work enqueued so far on `from` (nothing when they are
+// the same stream).
+bool order_after(cudaStream_t from, cudaStream_t to, cudaEvent_t ev) {
+  if (from == to) return true;
+  return cudaEventRecord(ev, from) == cudaSuccess && cudaStreamWaitEvent(to, ev, 0) == cudaSuccess;
+}
 
 
 bool valid_request(const rs_request& r) {
@@ -205,8 +242,7 @@ void CUDART_CB on_unit_done(void* p) {
 rs_status launch_single(rs_server* s, Unit* u) {
   Request& r = *u->members[0];
   const rs_request& q = r.req;
-  cudaStream_t st = (u->large && s->large_low_priority) ? s->streams_lo[u->stream]
-                                                        : s->streams[u->stream];
+  const Lanes ln = lanes_of(s, u);
   char* base = s->pool_base + u->pool_off;
   const size_t kbytes = q.n * q.key_bytes, vbytes = q.n * q.val_bytes;
   const SingleLayout L = single_layout(q);
@@ -216,24 +252,27 @@ rs_status launch_single(rs_server* s, Unit* u) {
   char* va = base + L.va;
   char* ws = base + L.ws;
   const size_t ws_bytes = L.ws_bytes;
-  if (cudaMemcpyAsync(k, q.h_keys, kbytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
+  if (cudaMemcpyAsync(k, q.h_keys, kbytes, cudaMemcpyHostToDevice, ln.in) != cudaSuccess)
     return RS_ERR_CUDA;
-  if (vbytes && cudaMemcpyAsync(v, q.h_vals, vbytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
+  if (vbytes && cudaMemcpyAsync(v, q.h_vals, vbytes, cudaMemcpyHostToDevice, ln.in) != cudaSuccess)
     return RS_ERR_CUDA;
+  if (!order_after(ln.in, ln.cs, s->ev_in[u->stream])) return RS_ERR_CUDA;
   int in_alt = 0;
   rs_status rs_st = rs_sort(q.key_bytes, q.val_bytes, k, vbytes ? v : nullptr, ka,
                             vbytes ? va : nullptr, q.n, q.begin_bit, q.end_bit, nullptr, ws,
-                            ws_bytes, reinterpret_cast<rs_stream_t>(st), &in_alt);
+                            ws_bytes, reinterpret_cast<rs_stream_t>(ln.cs), &in_alt);
   if (rs_st != RS_OK) return rs_st;
-  if (cudaMemcpyAsync(u->h_status, ws, sizeof(uint32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+  if (!order_after(ln.cs, ln.out, s->ev_sorted[u->stream])) return RS_ERR_CUDA;
+  if (cudaMemcpyAsync(u->h_status, ws, sizeof(uint32_t), cudaMemcpyDeviceToHost, ln.out) !=
+      cudaSuccess)
     return RS_ERR_CUDA;
-  if (cudaMemcpyAsync(q.h_out_keys, in_alt ? ka : k, kbytes, cudaMemcpyDeviceToHost, st) !=
+  if (cudaMemcpyAsync(q.h_out_keys, in_alt ? ka : k, kbytes, cudaMemcpyDeviceToHost, ln.out) !=
       cudaSuccess)
     return RS_ERR_CUDA;
   if (vbytes && cudaMemcpyAsync(q.h_out_vals, in_alt ? va : v, vbytes, cudaMemcpyDeviceToHost,
-                                st) != cudaSuccess)
+                                ln.out) != cudaSuccess)
     return RS_ERR_CUDA;
-  if (cudaLaunchHostFunc(st, on_unit_done, u) != cudaSuccess) return RS_ERR_CUDA;
+  if (cudaLaunchHostFunc(ln.out, on_unit_done, u) != cudaSuccess) return RS_ERR_CUDA;
   return RS_OK;
 }
 
@@ -261,7 +300,7 @@ BatchPlan plan_batch(const rs_request& q, size_t total, size_t nseg) {
 }
 
 rs_status launch_batch(rs_server* s, Unit* u, const BatchPlan& b) {
-  cudaStream_t st = s->streams[u->stream];
+  const Lanes ln = lanes_of(s, u);
   char* base = s->pool_base + u->pool_off;
   const size_t nseg = u->members.size();
   uint64_t* off = s->off_slab + size_t(u->stream) * (kMaxBatchMembers + 1);
@@ -273,32 +312,36 @@ rs_status launch_batch(rs_server* s, Unit* u, const BatchPlan& b) {
   const size_t kb = size_t(q0.key_bytes), vb = size_t(q0.val_bytes);
   for (size_t i = 0; i < nseg; ++i) {
     const rs_request& q = u->members[i]->req;
-    if (cudaMemcpyAsync(base + b.k + off[i] * kb, q.h_keys, q.n * kb, cudaMemcpyHostToDevice, st) ||
+    if (cudaMemcpyAsync(base + b.k + off[i] * kb, q.h_keys, q.n * kb, cudaMemcpyHostToDevice,
+                        ln.in) ||
         (vb && cudaMemcpyAsync(base + b.v + off[i] * vb, q.h_vals, q.n * vb,
-                               cudaMemcpyHostToDevice, st)))
+                               cudaMemcpyHostToDevice, ln.in)))
       return RS_ERR_CUDA;
   }
-  if (cudaMemcpyAsync(base + b.off, off, (nseg + 1) * 8, cudaMemcpyHostToDevice, st))
+  if (cudaMemcpyAsync(base + b.off, off, (nseg + 1) * 8, cudaMemcpyHostToDevice, ln.in))
     return RS_ERR_CUDA;
+  if (!order_after(ln.in, ln.cs, s->ev_in[u->stream])) return RS_ERR_CUDA;
   int in_alt = 0;
   rs_status rs_st = rs_segmented_sort(
       q0.key_bytes, q0.val_bytes, base + b.k, vb ? base + b.v : nullptr, base + b.ka,
       vb ? base + b.va : nullptr, b.total, reinterpret_cast<const uint64_t*>(base + b.off), nseg,
-      q0.begin_bit, q0.end_bit, base + b.ws, b.bytes - b.ws, reinterpret_cast<rs_stream_t>(st),
-      &in_alt);
+      q0.begin_bit, q0.end_bit, base + b.ws, b.bytes - b.ws,
+      reinterpret_cast<rs_stream_t>(ln.cs), &in_alt);
   if (rs_st != RS_OK) return rs_st;
-  if (cudaMemcpyAsync(u->h_status, base + b.ws, sizeof(uint32_t), cudaMemcpyDeviceToHost, st))
+  if (!order_after(ln.cs, ln.out, s->ev_sorted[u->stream])) return RS_ERR_CUDA;
+  if (cudaMemcpyAsync(u->h_status, base + b.ws, sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                      ln.out))
     return RS_ERR_CUDA;
   const size_t ko = in_alt ? b.ka : b.k, vo = in_alt ? b.va : b.v;
   for (size_t i = 0; i < nseg; ++i) {
     const rs_request& q = u->members[i]->req;
     if (cudaMemcpyAsync(q.h_out_keys, base + ko + off[i] * kb, q.n * kb, cudaMemcpyDeviceToHost,
-                        st) ||
+                        ln.out) ||
         (vb && cudaMemcpyAsync(q.h_out_vals, base + vo + off[i] * vb, q.n * vb,
-                               cudaMemcpyDeviceToHost, st)))
+                               cudaMemcpyDeviceToHost, ln.out)))
       return RS_ERR_CUDA;
   }
-  if (cudaLaunchHostFunc(st, on_unit_done, u) != cudaSuccess) return RS_ERR_CUDA;
+  if (cudaLaunchHostFunc(ln.out, on_unit_done, u) != cudaSuccess) return RS_ERR_CUDA;
   return RS_OK;
 }
 
@@ -422,6 +465,7 @@ void scheduler(rs_server* s) {
         u->pool_off = off;
         u->pool_bytes = rs::align_up(b.bytes, 256);
         u->stream = si;
+        u->shared_copies = s->shared_copy_queues != 0;
         u->h_status = s->status_slab + si;
         *u->h_status = 0u;
         s->stream_busy[si] = 1;
@@ -467,6 +511,8 @@ void scheduler(rs_server* s) {
       u->pool_off = off;
       u->pool_bytes = rs::align_up(std::max<size_t>(need, 256), 256);
       u->stream = si;
+      u->low_priority = large && s->large_low_priority != 0;
+      u->shared_copies = s->shared_copy_queues != 0;
       u->h_status = s->status_slab + si;
       *u->h_status = 0u;
       s->stream_busy[si] = 1;
@@ -484,10 +530,37 @@ void scheduler(rs_server* s) {
     for (size_t i = 0; i < launches.size(); ++i)
       res[i] = launches[i].batch ? launch_batch(s, launches[i].u, launches[i].plan)
                                  : launch_single(s, launches[i].u);
+    for (size_t i = 0; i < launches.size(); ++i)
+      if (res[i] != RS_OK) {
+        // copies or kernels of the unit may already be queued: let them
+        // finish before its pool range and slot are handed out again
+        const Lanes ln = lanes_of(s, launches[i].u);
+        cudaStreamSynchronize(ln.in);
+        cudaStreamSynchronize(ln.cs);
+        cudaStreamSynchronize(ln.out);
+        cudaGetLastError();
+      }
     lk.lock();
     for (size_t i = 0; i < launches.size(); ++i)
       if (res[i] != RS_OK) finish_unit(s, launches[i].u, res[i]);
   }
+}
+
+// Streams, events, the pool and the pinned slabs of a server (whichever exist).
+void release_cuda(rs_server* s) {
+  for (auto* v : {&s->streams, &s->streams_lo})
+    for (auto& t : *v)
+      if (t) cudaStreamDestroy(t);
+  for (auto* v : {&s->ev_in, &s->ev_sorted})
+    for (auto& e : *v)
+      if (e) cudaEventDestroy(e);
+  for (int c = 0; c < 2; ++c) {
+    if (s->copy_in[c]) cudaStreamDestroy(s->copy_in[c]);
+    if (s->copy_out[c]) cudaStreamDestroy(s->copy_out[c]);
+  }
+  if (s->pool_base) cudaFree(s->pool_base);
+  if (s->status_slab) cudaFreeHost(s->status_slab);
+  if (s->off_slab) cudaFreeHost(s->off_slab);
 }
 
 }  // namespace
@@ -525,26 +598,29 @@ rs_status rs_server_create(size_t budget_bytes, int streams, rs_server** out) {
   s->streams.assign(streams, nullptr);
   s->streams_lo.assign(streams, nullptr);
   s->stream_busy.assign(streams, 0);
+  s->ev_in.assign(streams, nullptr);
+  s->ev_sorted.assign(streams, nullptr);
   int least = 0, greatest = 0;  // numerically: greatest < least
   if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
     cudaGetLastError();
     least = greatest = 0;
   }
-  for (int i = 0; i < streams; ++i) {
-    if (cudaStreamCreateWithPriority(&s->streams[i], cudaStreamNonBlocking, greatest) !=
-            cudaSuccess ||
-        cudaStreamCreateWithPriority(&s->streams_lo[i], cudaStreamNonBlocking, least) !=
-            cudaSuccess) {
-      cudaGetLastError();
-      for (auto* v : {&s->streams, &s->streams_lo})
-        for (auto& t : *v)
-          if (t) cudaStreamDestroy(t);
-      cudaFree(s->pool_base);
-      cudaFreeHost(s->status_slab);
-      cudaFreeHost(s->off_slab);
-      delete s;
-      return RS_ERR_CUDA;
-    }
+  bool ok = true;
+  for (int i = 0; i < streams && ok; ++i)
+    ok = cudaStreamCreateWithPriority(&s->streams[i], cudaStreamNonBlocking, greatest) ==
+             cudaSuccess &&
+         cudaStreamCreateWithPriority(&s->streams_lo[i], cudaStreamNonBlocking, least) ==
+             cudaSuccess &&
+         cudaEventCreateWithFlags(&s->ev_in[i], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&s->ev_sorted[i], cudaEventDisableTiming) == cudaSuccess;
+  for (int c = 0; c < 2 && ok; ++c)
+    ok = cudaStreamCreateWithFlags(&s->copy_in[c], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaStreamCreateWithFlags(&s->copy_out[c], cudaStreamNonBlocking) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    release_cuda(s);
+    delete s;
+    return RS_ERR_CUDA;
   }
   s->sched = std::thread(scheduler, s);
   *out = s;
@@ -568,11 +644,7 @@ rs_status rs_server_destroy(rs_server* s) {
   }
   s->cv.notify_all();
   if (s->sched.joinable()) s->sched.join();
-  for (auto& st : s->streams) cudaStreamDestroy(st);
-  for (auto& st : s->streams_lo) cudaStreamDestroy(st);
-  cudaFree(s->pool_base);
-  cudaFreeHost(s->status_slab);
-  cudaFreeHost(s->off_slab);
+  release_cuda(s);
   delete s;
   return RS_OK;
 }
@@ -585,6 +657,7 @@ rs_status rs_server_get_config(rs_server* s, rs_server_config* out) {
   out->large_n = s->large_n;
   out->max_large = s->max_large;
   out->large_low_priority = s->large_low_priority;
+  out->shared_copy_queues = s->shared_copy_queues;
   return RS_OK;
 }
 
@@ -592,7 +665,8 @@ rs_status rs_server_set_config(rs_server* s, const rs_server_config* c) {
   if (!s || !c) return RS_ERR_INVALID;
   if (c->batch_max_n > c->max_batch_keys || c->max_batch_keys > RS_MAX_N || c->large_n == 0 ||
       c->max_large < 1 || c->max_large > 64 ||
-      (c->large_low_priority != 0 && c->large_low_priority != 1))
+      (c->large_low_priority != 0 && c->large_low_priority != 1) ||
+      (c->shared_copy_queues != 0 && c->shared_copy_queues != 1))
     return RS_ERR_INVALID;
   {
     std::lock_guard<std::mutex> g(s->mu);
@@ -601,6 +675,7 @@ rs_status rs_server_set_config(rs_server* s, const rs_server_config* c) {
     s->large_n = c->large_n;
     s->max_large = c->max_large;
     s->large_low_priority = c->large_low_priority;
+    s->shared_copy_queues = c->shared_copy_queues;
     s->changes += 1;  // the scheduler looks at the queue again
   }
   s->cv.notify_all();

@@ -71,7 +71,7 @@ class rs_server_stats_t(ctypes.Structure):
 class rs_server_config(ctypes.Structure):
     _fields_ = [("batch_max_n", ctypes.c_size_t), ("max_batch_keys", ctypes.c_size_t),
                 ("large_n", ctypes.c_size_t), ("max_large", ctypes.c_int),
-                ("large_low_priority", ctypes.c_int)]
+                ("large_low_priority", ctypes.c_int), ("shared_copy_queues", ctypes.c_int)]
 
 
 class rs_sort_stats(ctypes.Structure):

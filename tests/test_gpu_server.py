@@ -215,8 +215,8 @@ def test_rejections_and_cancel():
 
 def test_config_policies_same_results():
     """Every scheduling policy gives the oracle's results: no batching, every
-    request large with one at a time, and large requests on default-priority
-    streams."""
+    request large with one at a time, large requests on default-priority
+    streams, and copies through the shared copy queues."""
     reqs = make_trace(40, seed=21, max_log2=17)
     st, srv = rs.rs_server_create(1 << 30, 4)
     rs.check(st)
@@ -224,15 +224,16 @@ def test_config_policies_same_results():
         st, cfg = rs.rs_server_get_config(srv)
         rs.check(st)
         assert cfg == {"batch_max_n": 1 << 14, "max_batch_keys": 1 << 22, "large_n": 1 << 21,
-                       "max_large": 3, "large_low_priority": 1}
+                       "max_large": 3, "large_low_priority": 1, "shared_copy_queues": 0}
         for bad in ({"batch_max_n": 1 << 23}, {"max_batch_keys": (1 << 30) + 1},
                     {"large_n": 0}, {"max_large": 0}, {"max_large": 65},
-                    {"large_low_priority": 2}):
+                    {"large_low_priority": 2}, {"shared_copy_queues": 2}):
             assert rs.rs_server_set_config(srv, dict(cfg, **bad)) == rs.RS_ERR_INVALID
         assert rs.rs_server_get_config(srv)[1] == cfg  # a rejected setting changes nothing
         for policy in ({"batch_max_n": 0},
                        {"large_n": 1, "max_large": 1},
-                       {"large_n": 1 << 12, "large_low_priority": 0}):
+                       {"large_n": 1 << 12, "large_low_priority": 0},
+                       {"large_n": 1 << 12, "shared_copy_queues": 1}):
             rs.check(rs.rs_server_set_config(srv, dict(cfg, **policy)), "rs_server_set_config")
             rs.check(rs.rs_server_reset_stats(srv))
             out = run(srv, reqs)

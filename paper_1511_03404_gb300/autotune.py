@@ -26,7 +26,9 @@ import numpy as np
 from . import rs
 
 TYPES = ((4, 0), (4, 4), (8, 0), (8, 8))
-SIZES = tuple(2**e for e in (12, 13, 14, 16, 18, 20, 22, 24, 26))
+# the lengths of the paper's grid (Sec. 3): 2^e and 2^e + 2^(e-1); a band per
+# half octave, so that no length of the grid falls between two measured sizes
+SIZES = tuple(sorted({2**e for e in range(12, 27)} | {2**e + 2**(e - 1) for e in range(12, 26)}))
 
 
 def _time_variant(torch, kb, vb, n, variant, keys, vals, reps):
@@ -96,7 +98,7 @@ def tune(sizes=SIZES, types=TYPES, reps=5, log=print, verbose=False) -> dict:
                             "gkeys_per_s": n / (results[best] / 1e3) / 1e9,
                             "candidates": {str(i): round(ms, 5) for i, ms in results.items()},
                             "variant_info": infos[best]})
-            log(f"k{kb} v{vb} n=2^{int(np.log2(n))}: best variant {best} "
+            log(f"k{kb} v{vb} n={n}: best variant {best} "
                 f"({infos[best]}) {results[best]:.4f} ms")
             del keys, vals
         torch.cuda.empty_cache()

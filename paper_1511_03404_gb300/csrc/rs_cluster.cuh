@@ -13,9 +13,13 @@
 //      (remote shared-memory stores); after a cluster barrier each CTA reads
 //      its own table: the start of digit d is the count of all smaller
 //      digits, plus the count of digit d in lower-ranked CTAs;
-//   3. each key (and value) is stored at its global position, in the
-//      destination buffer of the CTA that owns that position (a remote
-//      shared-memory store);
+//   3. the CTA first stages its keys (and values) in digit order in its own
+//      source buffer (its keys are in registers by then), then its threads
+//      take the staged keys in order and store each at its global position,
+//      in the destination buffer of the CTA that owns that position (a
+//      remote shared-memory store): consecutive threads store consecutive
+//      keys of a digit run to consecutive addresses of one CTA, instead of
+//      scattering single keys over the cluster;
 //   4. cluster barrier; the destination buffer becomes the next source.
 // Past the end of the array the slices hold the largest key, which sorts
 // after every real key in every pass and is never written out.  The
@@ -66,7 +70,8 @@ struct ClusterSmem {
   static constexpr int MAX_CL = 8;
   static constexpr int CNT = MM + WARPS * RADIX * 4;        // u32 [MAX_CL][RADIX] every CTA's counts
   static constexpr int BASE = CNT + MAX_CL * RADIX * 4;     // u32 [RADIX] global digit bases
-  static constexpr int TOT = BASE + RADIX * 4;              // u32 [32]
+  static constexpr int LST = BASE + RADIX * 4;              // u32 [RADIX] digit starts in the CTA
+  static constexpr int TOT = LST + RADIX * 4;               // u32 [32]
   static constexpr int KEYS = (TOT + 32 * 4 + 15) / 16 * 16;  // K [2][SLICE]
   static constexpr int VALS = KEYS + 2 * SLICE * KB;        // V [2][SLICE]
   static constexpr int BYTES = VALS + (VB > 0 ? 2 * SLICE * VB : 0);
@@ -84,6 +89,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint32_t* s_mm = reinterpret_cast<uint32_t*>(smem + S::MM);
   uint32_t* s_cnt = reinterpret_cast<uint32_t*>(smem + S::CNT);
   uint32_t* s_base = reinterpret_cast<uint32_t*>(smem + S::BASE);
+  uint32_t* s_lst = reinterpret_cast<uint32_t*>(smem + S::LST);
   uint32_t* s_tot = reinterpret_cast<uint32_t*>(smem + S::TOT);
   K* s_k = reinterpret_cast<K*>(smem + S::KEYS);
   V* s_v = reinterpret_cast<V*>(smem + S::VALS);
@@ -133,18 +139,30 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     warp_rank_packed<ITEMS>(dp, s_wh + warp * RADIX, s_mm + warp * RADIX, lane);
     __syncthreads();
+    uint32_t run = 0u;
     if (tid < RADIX) {
-      uint32_t run = 0u;
 #pragma unroll
       for (int w = 0; w < WARPS; ++w) {
         const uint32_t c = s_wh[w * RADIX + tid];
         s_wh[w * RADIX + tid] = run;
         run += c;
       }
-      // ---- 2. this CTA's counts into every CTA's table, then the digit bases
+      // ---- 2. this CTA's counts into every CTA's table
       for (uint32_t c = 0; c < ncta; ++c)
         st_cluster(map_shared(s_cnt + rank * RADIX + tid, c), run);
     }
+    // ---- 3a. the CTA's keys in digit order, staged in its source buffer
+    const uint32_t lstart = block_exclusive_scan<THREADS>(run, s_tot);
+    if (tid < RADIX) s_lst[tid] = lstart;
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+      const uint32_t d = dp[j] >> 16;
+      const uint32_t at = s_lst[d] + s_wh[warp * RADIX + d] + (dp[j] & 0xffffu);
+      ks[at] = key[j];
+      if constexpr (VB > 0) vs[at] = val[j];
+    }
+    // every CTA's counts have landed and the stage is complete
     cluster_sync_all();
     uint32_t total = 0u, below = 0u;
     if (tid < RADIX) {
@@ -155,18 +173,19 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
     }
     const uint32_t start = block_exclusive_scan<THREADS>(total, s_tot);
-    if (tid < RADIX) s_base[tid] = start + below;
+    // staged key i of digit d goes to global position s_base[d] + i
+    if (tid < RADIX) s_base[tid] = start + below - s_lst[tid];
     __syncthreads();
-    // ---- 3. remote scatter into the owners' destination buffers
+    // ---- 3b. remote stores of the staged runs into the owners' destination buffers
     K* kd = s_k + (src ^ 1) * SLICE;
     V* vd = s_v + (src ^ 1) * SLICE;
-#pragma unroll
-    for (int j = 0; j < ITEMS; ++j) {
-      const uint32_t d = dp[j] >> 16;
-      const uint32_t g = s_base[d] + s_wh[warp * RADIX + d] + (dp[j] & 0xffffu);
+#pragma unroll 4
+    for (int i = tid; i < SLICE; i += THREADS) {
+      const K k = ks[i];
+      const uint32_t g = s_base[digit_of(k, shift, mask)] + uint32_t(i);
       const uint32_t owner = g / uint32_t(SLICE), at = g % uint32_t(SLICE);
-      st_cluster(map_shared(kd + at, owner), key[j]);
-      if constexpr (VB > 0) st_cluster(map_shared(vd + at, owner), val[j]);
+      st_cluster(map_shared(kd + at, owner), k);
+      if constexpr (VB > 0) st_cluster(map_shared(vd + at, owner), vs[i]);
     }
     // ---- 4. the destination buffers are complete
     cluster_sync_all();

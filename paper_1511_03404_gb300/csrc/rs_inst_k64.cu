@@ -16,6 +16,9 @@ const Variant* variants_k64(int* count) {
       ClusterSort<uint64_t, 0, 8, 512, 16, 8>::describe(),
       OnesweepSort<uint64_t, 0, 8, 256, 13, 3, true, 16>::describe(),
       OnesweepSort<uint64_t, 0, 8, 256, 11, 3, true, 16>::describe(),
+      OnesweepSort<uint64_t, 0, 8, 256, 15, 3, true, 16, true>::describe(),
+      OnesweepSort<uint64_t, 0, 8, 256, 27, 2, true, 16, true>::describe(),
+      OnesweepSort<uint64_t, 0, 8, 256, 23, 2, true, 16>::describe(),
   };
   *count = int(sizeof(table) / sizeof(table[0]));
   return table;

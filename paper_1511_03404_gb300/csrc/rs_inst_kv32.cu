@@ -19,6 +19,9 @@ const Variant* variants_kv32(int* count) {
       ClusterSort<uint32_t, 4, 8, 512, 16, 8>::describe(),
       OnesweepSort<uint32_t, 4, 8, 256, 15, 4, true, 16>::describe(),
       OnesweepSort<uint32_t, 4, 8, 256, 17, 4, true, 16>::describe(),
+      OnesweepSort<uint32_t, 4, 8, 256, 33, 2, true, 16>::describe(),
+      OnesweepSort<uint32_t, 4, 8, 256, 41, 2, true, 16>::describe(),
+      OnesweepSort<uint32_t, 4, 8, 256, 45, 2, true, 16>::describe(),
   };
   *count = int(sizeof(table) / sizeof(table[0]));
   return table;

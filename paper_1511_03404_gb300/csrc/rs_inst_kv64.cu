@@ -16,6 +16,8 @@ const Variant* variants_kv64(int* count) {
       ClusterSort<uint64_t, 8, 8, 512, 8, 8>::describe(),
       OnesweepSort<uint64_t, 8, 8, 256, 13, 2, false, 16>::describe(),
       OnesweepSort<uint64_t, 8, 8, 256, 11, 2, false, 16>::describe(),
+      OnesweepSort<uint64_t, 8, 8, 256, 23, 2, true, 16>::describe(),
+      OnesweepSort<uint64_t, 8, 8, 256, 19, 2, true, 16>::describe(),
   };
   *count = int(sizeof(table) / sizeof(table[0]));
   return table;

@@ -426,9 +426,19 @@ __global__ void __launch_bounds__(THREADS, 1)
 
 // UNIT: lanes per ranking unit, 32 (a warp, warp_rank_packed) or 16 (half a
 // warp, half_rank_packed).
-template <class K, int VB, int RADIX_BITS, int THREADS, int ITEMS, int UNIT = 32>
+// Words of the zero source of the counter-clearing bulk copies: the counters
+// of up to 32 half-warp units (512 threads) x 256 digits.
+constexpr int kZeroWords = 8192;
+
+// INPLACE (keys only, half-warp units): the keys are staged in (digit, input)
+// order in the key buffer itself, which is free once every thread holds its
+// keys in registers; there is no separate stage, so the tile costs its keys'
+// bytes of shared memory once instead of twice.
+template <class K, int VB, int RADIX_BITS, int THREADS, int ITEMS, int UNIT = 32,
+          bool INPLACE = false>
 struct OnesweepSmem {
   static_assert(UNIT == 32 || UNIT == 16, "warp or half-warp ranking units");
+  static_assert(!INPLACE || (VB == 0 && UNIT == 16), "in-place stage: keys only, half-warp units");
   static constexpr int RADIX = 1 << RADIX_BITS;
   static constexpr int WARPS = THREADS / 32;
   static constexpr int UNITS = THREADS / UNIT;
@@ -437,7 +447,7 @@ struct OnesweepSmem {
   static constexpr int WH = 0;                              // u32 [UNITS][RADIX] unit counters
   // half-warp units: the counters are cleared by a bulk copy with each tile's keys
   static constexpr uint32_t ZERO_BYTES = UNIT == 16 ? uint32_t(UNITS * RADIX * 4) : 0u;
-  static_assert(ZERO_BYTES <= 4096 * 4 && ZERO_BYTES % 16 == 0, "one bulk copy of zeros");
+  static_assert(ZERO_BYTES <= kZeroWords * 4 && ZERO_BYTES % 16 == 0, "one bulk copy of zeros");
   static constexpr int CNT = WH + UNITS * RADIX * 4;       // u32 [RADIX] tile counts
   static constexpr int TSTART = CNT + RADIX * 4;           // u32 [RADIX] tile digit starts
   static constexpr int GBASE = TSTART + RADIX * 4;         // u32 [RADIX] global base
@@ -449,11 +459,11 @@ struct OnesweepSmem {
   static constexpr int KIN = (MBAR + 16 + 15) / 16 * 16;
   // the tile in (digit, input) order: keys, then values; during the rank of
   // warp units it holds the warps' peer masks (u32 [WARPS][RADIX])
-  static constexpr int OUT = KIN + TILE * ELEM + 16;
+  static constexpr int OUT = INPLACE ? KIN : KIN + TILE * ELEM + 16;
   static constexpr int MM = OUT;
   static constexpr int OUT_BYTES =
       TILE * ELEM > WARPS * RADIX * 4 ? TILE * ELEM : WARPS * RADIX * 4;
-  static constexpr int BYTES = OUT + OUT_BYTES;
+  static constexpr int BYTES = INPLACE ? KIN + TILE * ELEM + 16 : OUT + OUT_BYTES;
 };
 
 // Operands of one tile of one digit pass over one array (or one segment).
@@ -665,13 +675,13 @@ struct Stage {
 // Zeros in global memory, the source of the bulk copies that clear the rank
 // counters of a tile (one copy per TU; never written).
 namespace {
-__device__ __align__(128) uint32_t g_zero_words[4096];
+__device__ __align__(128) uint32_t g_zero_words[kZeroWords];
 }
 
 // Start staging the keys of tile `tile` of an array of n keys into the key
 // buffer: one bulk copy issued by thread 0 on `bar`, head/tail elements and
 // the past-the-end sentinels written by every thread.  zero_dst (optional):
-// zero_bytes (a multiple of 16, at most 16 KB) of shared memory cleared by a
+// zero_bytes (a multiple of 16, at most kZeroWords words) of shared memory cleared by a
 // second bulk copy on the same barrier, so that the tile's counters are zero
 // once its keys have landed, without a store loop on the shared-memory pipe.
 template <class K, int THREADS, int TILE, bool CG>
@@ -720,13 +730,13 @@ struct Prefetch {
 // id (s_misc[3]) and starts staging its keys (s_misc[4] = 1), overlapping the
 // end of this tile.
 template <class K, int VB, int RADIX_BITS, int THREADS, int ITEMS, bool CG, bool PERSIST = false,
-          int UNIT = 32>
+          int UNIT = 32, bool INPLACE = false>
 __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ctrl,
                                               uint64_t timeout_ns, unsigned char* smem,
                                               uint32_t parity = 0u,
                                               const Prefetch* pf = nullptr) {
   using V = ValT<VB>;
-  using S = OnesweepSmem<K, VB, RADIX_BITS, THREADS, ITEMS, UNIT>;
+  using S = OnesweepSmem<K, VB, RADIX_BITS, THREADS, ITEMS, UNIT, INPLACE>;
   constexpr int RADIX = S::RADIX, WARPS = S::WARPS, UNITS = S::UNITS, TILE = S::TILE;
   static_assert(RADIX <= THREADS, "one thread per digit");
   static_assert(TILE <= 65536, "stage slots fit 16 bits");
@@ -973,7 +983,7 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
   }
   stamp(t.trace, 4);
   // keys only: the key buffer is free (keys are staged in OUT) -- start the next tile
-  if constexpr (PERSIST && VB == 0) {
+  if constexpr (PERSIST && VB == 0 && !INPLACE) {
     if (tid == 0) {
       const uint32_t nxt = atomicAdd(pf->counter, 1u);
       s_misc[3] = nxt;
@@ -1025,6 +1035,19 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
     scatter_keys(std::true_type{});
   else
     scatter_keys(std::false_type{});
+  // in place: the key buffer is free once every staged key has left -- start the next tile
+  if constexpr (PERSIST && INPLACE) {
+    __syncthreads();
+    if (tid == 0) {
+      const uint32_t nxt = atomicAdd(pf->counter, 1u);
+      s_misc[3] = nxt;
+      s_misc[4] = nxt < pf->tiles ? 1u : 0u;
+    }
+    __syncthreads();
+    if (s_misc[4])
+      stage_keys<K, THREADS, TILE, CG>(smem + S::KIN, t.ksrc, n, s_misc[3], &s_bar[0],
+                                       smem + S::WH, S::ZERO_BYTES);
+  }
   stamp(t.trace, 5);
   bool ok = true;
   if constexpr (VB > 0) {
@@ -1077,14 +1100,15 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
 // One digit pass, one tile per CTA.  The grid has one CTA per tile; tile ids
 // come from an atomic counter so that a tile's predecessors have always
 // started before it (forward progress of the look-back).
-template <class K, int VB, int RADIX_BITS, int THREADS, int ITEMS, int MINB, int UNIT = 32>
+template <class K, int VB, int RADIX_BITS, int THREADS, int ITEMS, int MINB, int UNIT = 32,
+          bool INPLACE = false>
 __global__ void __launch_bounds__(THREADS, MINB)
     k_onesweep(K* __restrict__ k0, K* __restrict__ k1, ValT<VB>* __restrict__ v0,
                ValT<VB>* __restrict__ v1, uint32_t n, int pass, uint32_t shift, uint32_t mask,
                const uint32_t* __restrict__ pass_offsets, uint32_t* __restrict__ status,
                uint32_t* __restrict__ gagg, uint32_t* __restrict__ ginc, uint32_t tiles,
                Ctrl* __restrict__ ctrl, Knobs knobs, KeyXf<K> xf, bool early_dependents) {
-  using S = OnesweepSmem<K, VB, RADIX_BITS, THREADS, ITEMS, UNIT>;
+  using S = OnesweepSmem<K, VB, RADIX_BITS, THREADS, ITEMS, UNIT, INPLACE>;
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t* s_misc = reinterpret_cast<uint32_t*>(smem + S::MISC);
   pdl_wait();  // the kernel before (upsweep or previous pass) is complete
@@ -1129,8 +1153,8 @@ __global__ void __launch_bounds__(THREADS, MINB)
   t.xf = xf;
   t.xin = xf.on && pass == __ffs(int(exec)) - 1;  // first and last pass that move data
   t.xout = xf.on && pass == 31 - __clz(exec);
-  onesweep_tile<K, VB, RADIX_BITS, THREADS, ITEMS, false, false, UNIT>(t, ctrl, knobs.timeout_ns,
-                                                                      smem);
+  onesweep_tile<K, VB, RADIX_BITS, THREADS, ITEMS, false, false, UNIT, INPLACE>(
+      t, ctrl, knobs.timeout_ns, smem);
   __syncthreads();
   if (threadIdx.x == 0) atomicMax(&ctrl->t_pass[pass][1], stat_now(ctrl));
 }
@@ -1140,7 +1164,8 @@ __global__ void __launch_bounds__(THREADS, MINB)
 // loading its next tile while it finishes the current one.  Tile ids are
 // still taken in order by running CTAs, so the look-back keeps making
 // progress: the lowest unfinished tile is always being worked on.
-template <class K, int VB, int RADIX_BITS, int THREADS, int ITEMS, int MINB, int UNIT = 32>
+template <class K, int VB, int RADIX_BITS, int THREADS, int ITEMS, int MINB, int UNIT = 32,
+          bool INPLACE = false>
 __global__ void __launch_bounds__(THREADS, MINB)
     k_onesweep_persist(K* __restrict__ k0, K* __restrict__ k1, ValT<VB>* __restrict__ v0,
                        ValT<VB>* __restrict__ v1, uint32_t n, int pass, uint32_t shift,
@@ -1148,7 +1173,7 @@ __global__ void __launch_bounds__(THREADS, MINB)
                        uint32_t* __restrict__ status, uint32_t* __restrict__ gagg,
                        uint32_t* __restrict__ ginc, uint32_t tiles, Ctrl* __restrict__ ctrl,
                        Knobs knobs, KeyXf<K> xf, bool early_dependents) {
-  using S = OnesweepSmem<K, VB, RADIX_BITS, THREADS, ITEMS, UNIT>;
+  using S = OnesweepSmem<K, VB, RADIX_BITS, THREADS, ITEMS, UNIT, INPLACE>;
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t* s_misc = reinterpret_cast<uint32_t*>(smem + S::MISC);
   uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem + S::MBAR);
@@ -1202,7 +1227,7 @@ __global__ void __launch_bounds__(THREADS, MINB)
     t.trace = (knobs.trace != nullptr && pass == knobs.trace_pass && tile < knobs.trace_tiles)
                   ? knobs.trace + size_t(tile) * 16
                   : nullptr;
-    const bool ok = onesweep_tile<K, VB, RADIX_BITS, THREADS, ITEMS, false, true, UNIT>(
+    const bool ok = onesweep_tile<K, VB, RADIX_BITS, THREADS, ITEMS, false, true, UNIT, INPLACE>(
         t, ctrl, knobs.timeout_ns, smem, it & 1u, &pf);
     __syncthreads();
     const bool next = s_misc[4] != 0u;

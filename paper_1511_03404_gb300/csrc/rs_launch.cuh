@@ -15,15 +15,15 @@ namespace rs {
 
 // PERSIST: the passes run as k_onesweep_persist on a grid of SMs x resident
 // CTAs instead of one CTA per tile.  UNIT: lanes per ranking unit (32: warps,
-// 16: half warps).
+// 16: half warps).  INPLACE: keys only, staged in the key buffer itself.
 template <class K, int VB, int R, int THREADS, int ITEMS, int MINB, bool PERSIST = false,
-          int UNIT = 32>
+          int UNIT = 32, bool INPLACE = false>
 struct OnesweepSort {
   static constexpr int RADIX = 1 << R;
   static constexpr int TILE = THREADS * ITEMS;
   static constexpr int UP_THREADS = 1024;
   static constexpr int MAXP = (8 * int(sizeof(K)) + R - 1) / R;
-  using S = OnesweepSmem<K, VB, R, THREADS, ITEMS, UNIT>;
+  using S = OnesweepSmem<K, VB, R, THREADS, ITEMS, UNIT, INPLACE>;
 
   static size_t tiles(uint32_t n) { return (size_t(n) + TILE - 1) / TILE; }
 
@@ -71,8 +71,10 @@ struct OnesweepSort {
     const Layout L = onesweep_layout(passes, R, nt);
     using V = ValT<VB>;
     auto kern = [] {  // instantiate only the kernel this variant launches
-      if constexpr (PERSIST) return &k_onesweep_persist<K, VB, R, THREADS, ITEMS, MINB, UNIT>;
-      else return &k_onesweep<K, VB, R, THREADS, ITEMS, MINB, UNIT>;
+      if constexpr (PERSIST)
+        return &k_onesweep_persist<K, VB, R, THREADS, ITEMS, MINB, UNIT, INPLACE>;
+      else
+        return &k_onesweep<K, VB, R, THREADS, ITEMS, MINB, UNIT, INPLACE>;
     }();
     const int occ = prepare_kernel(reinterpret_cast<const void*>(kern), THREADS, S::BYTES);
     if (occ <= 0) return cudaErrorInvalidConfiguration;

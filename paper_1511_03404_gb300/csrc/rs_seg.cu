@@ -12,10 +12,10 @@ namespace rs {
 
 namespace {
 
-// MINB: resident CTAs per SM the pass and short-segment kernels are compiled
-// for (their register budget).
+// MINB: resident CTAs per SM the short-segment kernel is compiled for (its
+// register budget); PASS_MINB: the same for the pass kernel.
 template <class K, int VB, int R, int THREADS, int ITEMS, int CHUNK_TILES, int UNIT,
-          int SMALL_ITEMS, int MINB = 4>
+          int SMALL_ITEMS, int MINB = 4, int PASS_MINB = MINB>
 struct SegSort {
   using C = SegKernelCfg<K, VB, R, THREADS, ITEMS, CHUNK_TILES, UNIT, SMALL_ITEMS>;
   static constexpr int PLAN_THREADS = 1024;
@@ -50,7 +50,7 @@ struct SegSort {
     const int occ_hist =
         prepare_kernel(reinterpret_cast<const void*>(hist), C::HIST_THREADS, C::HIST_BYTES);
     if (occ_hist <= 0) return cudaErrorInvalidConfiguration;
-    auto kern = &k_seg_persistent<K, VB, R, THREADS, ITEMS, CHUNK_TILES, UNIT, MINB>;
+    auto kern = &k_seg_persistent<K, VB, R, THREADS, ITEMS, CHUNK_TILES, UNIT, PASS_MINB>;
     const int occ = prepare_kernel(reinterpret_cast<const void*>(kern), THREADS, C::BYTES);
     if (occ <= 0) return cudaErrorInvalidConfiguration;
     SegArgs a;
@@ -97,18 +97,16 @@ struct SegSort {
   }
 };
 
-// u32 pairs: pass tiles of 256 x 17 keys ranked in half-warp units; short
-// segments up to 4096 elements sorted whole by one CTA
-using SegU32Pairs = SegSort<uint32_t, 4, 8, 256, 17, 32, 16, 16>;
-// u32 keys: 256 x 13 keys in half-warp units (the keys stay in registers from
-// the rank to the stage, which 16 keys per thread would spill at four CTAs per
-// SM; an odd count keeps the two halves of a warp 16 banks apart); short
+// u32 pairs: pass tiles of 256 x 45 keys ranked in half-warp units, two CTAs
+// per SM; short segments up to 4096 elements sorted whole by one CTA
+using SegU32Pairs = SegSort<uint32_t, 4, 8, 256, 45, 12, 16, 16, 4, 2>;
+// u32 keys: 256 x 37 keys in half-warp units, two CTAs per SM; short
 // segments up to 4096
-using SegU32Keys = SegSort<uint32_t, 0, 8, 256, 13, 32, 16, 16>;
-// 64-bit keys and pairs: 256 x 8 elements, short segments up to 2048; pairs
-// at three CTAs per SM (their registers)
-using SegU64Keys = SegSort<uint64_t, 0, 8, 256, 8, 32, 32, 8>;
-using SegU64Pairs = SegSort<uint64_t, 8, 8, 256, 8, 32, 32, 8, 3>;
+using SegU32Keys = SegSort<uint32_t, 0, 8, 256, 37, 16, 16, 16, 4, 2>;
+// 64-bit keys and pairs: 256 x 23 elements in half-warp units, two CTAs per
+// SM; short segments up to 2048 (pairs: that kernel at three CTAs per SM)
+using SegU64Keys = SegSort<uint64_t, 0, 8, 256, 23, 24, 16, 8, 4, 2>;
+using SegU64Pairs = SegSort<uint64_t, 8, 8, 256, 23, 24, 16, 8, 3, 2>;
 
 bool seg_types(int kb, int vb) { return (kb == 4 || kb == 8) && (vb == 0 || vb == kb); }
 

@@ -424,12 +424,12 @@ __global__ void __launch_bounds__(THREADS, 1)
 
 // -------------------------------------------------------------- onesweep
 
-// UNIT: lanes per ranking unit, 32 (a warp, warp_rank_packed) or 16 (half a
-// warp, half_rank_packed).
 // Words of the zero source of the counter-clearing bulk copies: the counters
 // of up to 32 half-warp units (512 threads) x 256 digits.
 constexpr int kZeroWords = 8192;
 
+// UNIT: lanes per ranking unit, 32 (a warp, warp_rank_packed) or 16 (half a
+// warp, half_rank_packed).
 // INPLACE (keys only, half-warp units): the keys are staged in (digit, input)
 // order in the key buffer itself, which is free once every thread holds its
 // keys in registers; there is no separate stage, so the tile costs its keys'

@@ -894,7 +894,7 @@ __device__ __forceinline__ bool onesweep_tile(const TileArgs<K, VB>& t, Ctrl* ct
         }
       } else {
         const int32_t g = int32_t(tile / kGroupTiles);
-        walk_tiles<RADIX, 2>(t.status, tid, int32_t(tile) - 1, g * kGroupTiles, excl, done,
+        walk_tiles<RADIX, 1>(t.status, tid, int32_t(tile) - 1, g * kGroupTiles, excl, done,
                              gave_up, ctrl, timeout_ns, tile, t.trace);
         stamp(t.trace, 14);
         // earlier groups, 8 per round trip (two 16-byte loads per array)

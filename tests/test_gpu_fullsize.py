@@ -196,6 +196,35 @@ def check_pairs_order(src, out_k, out_v, o):
 
 @pytest.mark.parametrize("kind,descending", [(1, False), (1, True), (2, False), (2, True)],
                          ids=["signed", "signed_desc", "float", "float_desc"])
+def test_u64_keys_2p26_key_orders(kind, descending):
+    """64-bit keys only in the signed and IEEE-754 orders, ascending and
+    descending, at 2^26 (the tuned pass stages these keys in place): the
+    output is the sorted multiset of the input under that order."""
+    n = 1 << 26
+    k = inputs.keys(np.uint64, "uniform", n) if kind == 1 else inputs.float_keys(np.uint64, n)
+    dk = to_dev(k, torch)
+    src = dk.clone()
+    ka = torch.empty_like(dk)
+    st, need = rs.rs_workspace_bytes(8, 0, n, 0, 64)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    h = torch.cuda.current_stream().cuda_stream
+    st, in_alt = rs.rs_sort(8, 0, dk.data_ptr(), None, ka.data_ptr(), None, n, 0, 64,
+                            ws.data_ptr(), ws.numel(), h, key_kind=kind, descending=descending)
+    rs.check(st, "rs_sort")
+    rs.check(rs.rs_workspace_status(ws.data_ptr(), h)[0], "device status")
+    out_k = ka if in_alt else dk
+
+    def order(t):  # signed int64 whose order is the requested one
+        o = t if kind == 1 else t ^ ((t >> 63) & 0x7FFFFFFFFFFFFFFF)
+        return ~o if descending else o
+
+    o = order(out_k)
+    assert bool((o[1:] >= o[:-1]).all()), "keys not in order"
+    assert torch.equal(o, torch.sort(order(src)).values), "not the input's multiset"
+
+
+@pytest.mark.parametrize("kind,descending", [(1, False), (1, True), (2, False), (2, True)],
+                         ids=["signed", "signed_desc", "float", "float_desc"])
 def test_u32_pairs_2p26_key_orders(kind, descending):
     """Signed and IEEE-754 orders, ascending and descending, at the benchmark
     size: stable in every mode (equal keys keep their input order)."""

@@ -28,3 +28,18 @@ def test_extend_to_max_skips_bounded_variants_and_missing_types():
     assert len(entries) == 1
     autotune.extend_to_max(entries, 8, 8, infos)  # no entries of that type
     assert len(entries) == 1
+
+
+def test_tuned_sizes_cover_the_paper_grid():
+    """Every length of the paper's grid (Sec. 3: 2^e and 2^e + 2^(e-1)) is a
+    measured size of the autotuner, so that no length the sweep reports falls
+    between two tuned bands; and the committed table has an entry at each."""
+    import json
+    from paper_1511_03404_gb300 import sweep
+    grid = set(sweep.lengths(4)) | set(sweep.lengths(8))
+    assert grid <= set(autotune.SIZES)
+    with open(rs.TUNED_TABLE) as f:
+        table = json.load(f)
+    for kb, vb in autotune.TYPES:
+        have = {e["n_max"] for e in table["entries"] if (e["key_bytes"], e["val_bytes"]) == (kb, vb)}
+        assert set(sweep.lengths(kb)) <= have, (kb, vb)

@@ -136,7 +136,9 @@ rs_status rs_variant_info(int key_bytes, int val_bytes, int index, int* radix_bi
  * entry falls back to the built-in choice).  Setting an existing n_max
  * replaces its variant.  RS_ERR_INVALID for an unknown type or variant.
  * Workspace sizes follow the table: query rs_workspace_bytes after changing
- * it.  rs_tune_clear drops every entry.
+ * it.  rs_tune_clear drops every entry.  The library starts with the
+ * package's tuned table as it was when the library was built (tuned.json),
+ * unless the environment sets RS_NO_TUNED_TABLE when the table is first used.
  */
 rs_status rs_tune_set(int key_bytes, int val_bytes, size_t n_max, int variant);
 rs_status rs_tune_clear(void);

@@ -7,6 +7,10 @@ include/rs.h.  A stamp of the sources and flags skips rebuilds.
 The debug flavour (_build/librs_debug.so, compiled with RS_DEBUG) checks the
 index of every global store of its kernels (rs_debug_status); the binding
 loads it instead of librs.so when the environment sets RS_LIBRARY=debug.
+
+The package's tuned variant table (tuned.json) is compiled into the library
+as its default table (_build/rs_tuned_table.inc), so that callers of the C
+ABI get the tuned choices without the binding.
 """
 from __future__ import annotations
 
@@ -24,6 +28,8 @@ LIB_PATH = os.path.join(OUT_DIR, "librs.so")
 DEBUG_LIB_PATH = os.path.join(OUT_DIR, "librs_debug.so")
 DEBUG_FLAGS = ("-DRS_DEBUG",)
 INCLUDE = os.path.join(ROOT, "include")
+TUNED_JSON = os.path.join(HERE, "tuned.json")
+TUNED_INC = os.path.join(OUT_DIR, "rs_tuned_table.inc")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2",
@@ -46,6 +52,8 @@ def _stamp(extra=()) -> str:
     files = sources() + sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC)
                                if f.endswith((".h", ".cuh")))
     files.append(os.path.join(INCLUDE, "rs.h"))
+    if os.path.exists(TUNED_JSON):
+        files.append(TUNED_JSON)
     for f in files:
         h.update(f.encode())
         with open(f, "rb") as fh:
@@ -56,13 +64,33 @@ def _stamp(extra=()) -> str:
 
 def _compile(src: str, extra, suffix: str = ".o") -> str:
     obj = os.path.join(OUT_DIR, os.path.basename(src) + suffix)
-    cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *extra, "-I", INCLUDE, "-c", src, "-o", obj]
+    cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *extra, "-I", INCLUDE, "-I", OUT_DIR, "-c", src, "-o", obj]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{res.stdout}\n{res.stderr}")
     if "spill" in (res.stderr or "") and "0 bytes spill" not in res.stderr:
         print(res.stderr)
     return obj
+
+
+def write_tuned_table(json_path: str = TUNED_JSON, out_path: str = TUNED_INC) -> int:
+    """Write the entries of the tuned table as C initialisers
+    ``{key_bytes, val_bytes, n_max, variant},`` (none when there is no table).
+    Returns the number of entries written."""
+    import json
+    entries = []
+    if os.path.exists(json_path):
+        with open(json_path) as f:
+            entries = json.load(f).get("entries", [])
+    lines = ["// written by the build step from tuned.json; not edited by hand"]
+    for e in entries:
+        lines.append("{%d, %d, %dull, %d}," % (int(e["key_bytes"]), int(e["val_bytes"]),
+                                              int(e["n_max"]), int(e["variant"])))
+    tmp = out_path + f".tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        f.write("\n".join(lines) + "\n")
+    os.replace(tmp, out_path)
+    return len(entries)
 
 
 def _flavours(debug: bool | None):
@@ -87,6 +115,7 @@ def build(force: bool = False, extra_flags=(), jobs: int | None = None,
                     continue
         todo.append((lib, stamp_path, stamp, suffix, tuple(extra_flags) + flags))
     if todo:
+        write_tuned_table()
         srcs = sources()
         units = [(src, t) for t in todo for src in srcs]
         jobs = jobs or min(len(units), max(1, os.cpu_count() or 1))

@@ -199,10 +199,53 @@ struct TuneEntry {
 };
 std::mutex g_tune_mu;
 std::map<int, std::vector<TuneEntry>> g_tune;  // key: key_bytes * 16 + val_bytes
+std::once_flag g_tune_defaults;
+
+// The package's tuned table as it stood when the library was built (the
+// build step writes it from tuned.json), so that C callers get the tuned
+// choices without the Python binding.
+struct TunedDefault {
+  int key_bytes, val_bytes;
+  unsigned long long n_max;
+  int variant;
+};
+const TunedDefault kTunedDefault[] = {
+#include "rs_tuned_table.inc"
+    {0, 0, 0ull, -1}};
+
+// caller holds g_tune_mu
+bool tune_set_locked(int key_bytes, int val_bytes, size_t n_max, int variant) {
+  int count = 0;
+  const Variant* v = variants(key_bytes, val_bytes, &count);
+  if (!v || variant < 0 || variant >= count) return false;
+  auto& list = g_tune[key_bytes * 16 + val_bytes];
+  bool replaced = false;
+  for (TuneEntry& e : list)
+    if (e.n_max == n_max) {
+      e.variant = variant;
+      replaced = true;
+    }
+  if (!replaced) list.push_back(TuneEntry{n_max, variant});
+  std::sort(list.begin(), list.end(),
+            [](const TuneEntry& a, const TuneEntry& b) { return a.n_max < b.n_max; });
+  return true;
+}
+
+// Install the built-in table once, before the table is first read or
+// changed (not when the environment sets RS_NO_TUNED_TABLE).
+void tune_defaults_once() {
+  std::call_once(g_tune_defaults, [] {
+    if (std::getenv("RS_NO_TUNED_TABLE")) return;
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    for (const TunedDefault& d : kTunedDefault)
+      if (d.variant >= 0) tune_set_locked(d.key_bytes, d.val_bytes, size_t(d.n_max), d.variant);
+  });
+}
 }  // namespace
 
 // The tuned variant for n elements of (kb, vb), or -1.
 static int tuned_variant(int kb, int vb, size_t n) {
+  tune_defaults_once();
   std::lock_guard<std::mutex> g(g_tune_mu);
   auto it = g_tune.find(kb * 16 + vb);
   if (it == g_tune.end()) return -1;
@@ -603,24 +646,13 @@ rs_status rs_profile_end(int* launches, double* ms, double* bytes) {
 }
 
 rs_status rs_tune_set(int key_bytes, int val_bytes, size_t n_max, int variant) {
-  int count = 0;
-  const Variant* v = variants(key_bytes, val_bytes, &count);
-  if (!v || variant < 0 || variant >= count) return RS_ERR_INVALID;
+  tune_defaults_once();
   std::lock_guard<std::mutex> g(g_tune_mu);
-  auto& list = g_tune[key_bytes * 16 + val_bytes];
-  bool replaced = false;
-  for (TuneEntry& e : list)
-    if (e.n_max == n_max) {
-      e.variant = variant;
-      replaced = true;
-    }
-  if (!replaced) list.push_back(TuneEntry{n_max, variant});
-  std::sort(list.begin(), list.end(),
-            [](const TuneEntry& a, const TuneEntry& b) { return a.n_max < b.n_max; });
-  return RS_OK;
+  return tune_set_locked(key_bytes, val_bytes, n_max, variant) ? RS_OK : RS_ERR_INVALID;
 }
 
 rs_status rs_tune_clear(void) {
+  tune_defaults_once();
   std::lock_guard<std::mutex> g(g_tune_mu);
   g_tune.clear();
   return RS_OK;

@@ -179,3 +179,50 @@ def test_typed_segmented_sort_checks_arguments_without_gpu():
                                 None)[0] == rs.RS_ERR_INVALID
     assert rs.rs_segmented_sort(4, 0, fake, None, fake, None, 100, fake, 2, 0, 32, None, 0,
                                 None)[0] == rs.RS_ERR_INVALID
+
+
+_DEFAULT_TABLE_PROBE = r"""
+import ctypes, json, sys
+sys.path.insert(0, sys.argv[1])
+from paper_1511_03404_gb300 import _build, rs
+lib = ctypes.CDLL(_build.LIB_PATH)  # the library alone: the binding installs nothing
+lib.rs_workspace_bytes.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_size_t, ctypes.c_int,
+                                   ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]
+def ws(kb, vb, n, variant=-1):
+    out = ctypes.c_size_t()
+    cfg = None if variant < 0 else ctypes.byref(rs.rs_config(0, variant, 0, 0))
+    assert lib.rs_workspace_bytes(kb, vb, n, 0, 8 * kb, cfg, ctypes.byref(out)) == 0
+    return out.value
+table = json.load(open(rs.TUNED_TABLE))
+rows = []
+for e in table["entries"]:
+    if e.get("ms") is None:
+        continue
+    n = int(e["n_max"])
+    rows.append([ws(e["key_bytes"], e["val_bytes"], n), ws(e["key_bytes"], e["val_bytes"], n, e["variant"])])
+print(json.dumps(rows))
+"""
+
+
+def _default_table_rows(env_extra):
+    import json
+    import subprocess
+    import sys
+    env = {k: v for k, v in os.environ.items() if k != "RS_NO_TUNED_TABLE"}
+    env.update(env_extra)
+    res = subprocess.run([sys.executable, "-c", _DEFAULT_TABLE_PROBE, ROOT], capture_output=True,
+                         text=True, env=env, timeout=300)
+    assert res.returncode == 0, res.stderr[-2000:]
+    return json.loads(res.stdout.strip().splitlines()[-1])
+
+
+def test_library_starts_with_the_tuned_table():
+    """A C caller that never installs a table gets the tuned choices: with no
+    configuration, every tuned size sorts with the table's variant (seen
+    through its workspace size), which the build compiled in from
+    tuned.json; RS_NO_TUNED_TABLE turns the built-in table off."""
+    rows = _default_table_rows({})
+    assert rows and all(default == tuned for default, tuned in rows)
+    off = _default_table_rows({"RS_NO_TUNED_TABLE": "1"})
+    # without the table the built-in choice differs from the tuned one somewhere
+    assert any(default != tuned for default, tuned in off)
